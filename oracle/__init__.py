@@ -1,0 +1,143 @@
+"""CPU oracle for the ordered greedy code sweep -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does; it
+shares no code with it.
+
+The arithmetic lives in ``greedy_oracle.c`` (plain C, compiled with gcc into
+``oracle/_build/liboracle.so``); this module only compiles it, loads it with
+ctypes and marshals numpy arrays.  Each function cites the passage it follows
+in the C file's header.
+
+Parity status of each function (the pins are in ``tests/test_oracle.py``):
+  order_list / order_sorted  pinned (definitions by comparator, Gray by the
+                             reflected construction, brute force)
+  greedy_pairwise (O1)       pinned (Example 1 of Section 4.1, Hamming and Golay
+                             codes of Section 7, brute force over all subsets)
+  greedy_ball (O2)           pinned (equal to O1 wherever O1 runs; Hamming
+                             [31,26,3] closed form)
+  verify (O3)                pinned (brute force: accepts exactly one subset)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+LEX, GRAY, GRLEX, GREVLEX = 0, 1, 2, 3
+ORDERS = {"lex": LEX, "gray": GRAY, "grlex": GRLEX, "grevlex": GREVLEX}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "greedy_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: no -march, no intrinsics)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC],
+                       check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32, u32p, i64p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+            lib.orc_candidate_count.restype = ctypes.c_uint64
+            lib.orc_candidate_count.argtypes = [i32, i32]
+            lib.orc_order_list.restype = i64
+            lib.orc_order_list.argtypes = [i32, i32, i32, u32p, i64]
+            lib.orc_order_sorted.restype = i64
+            lib.orc_order_sorted.argtypes = [i32, i32, i32, u32p, i64]
+            for f in (lib.orc_greedy_pairwise, lib.orc_greedy_ball):
+                f.restype = i64
+                f.argtypes = [i32, i32, i32, i32, u32p, i64p, i64]
+            lib.orc_verify.restype = i32
+            lib.orc_verify.argtypes = [i32, i32, i32, i32, u32p, i64]
+            lib.orc_distance.restype = i32
+            lib.orc_distance.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            _lib = lib
+    return _lib
+
+
+def _ord(ordering) -> int:
+    return ORDERS[ordering] if isinstance(ordering, str) else int(ordering)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def candidate_count(n: int, w: int = -1) -> int:
+    return int(_load().orc_candidate_count(n, w))
+
+
+def order_list(n: int, ordering, w: int = -1) -> np.ndarray:
+    """Candidates in order, streaming form (Section 4.2)."""
+    cnt = candidate_count(n, w)
+    out = np.empty(cnt, dtype=np.uint32)
+    k = _load().orc_order_list(n, _ord(ordering), w, _ptr(out), cnt)
+    if k != cnt:
+        raise RuntimeError(f"order_list returned {k}, expected {cnt}")
+    return out
+
+
+def order_sorted(n: int, ordering, w: int = -1) -> np.ndarray:
+    """Candidates in order by comparator sort over the whole space (n <= 24)."""
+    cnt = candidate_count(n, w)
+    out = np.empty(cnt, dtype=np.uint32)
+    k = _load().orc_order_sorted(n, _ord(ordering), w, _ptr(out), cnt)
+    if k != cnt:
+        raise RuntimeError(f"order_sorted returned {k}, expected {cnt}")
+    return out
+
+
+def _greedy(fn, n, d, ordering, w, with_pos):
+    lib = _load()
+    cap = min(candidate_count(n, w), 1 << 26)
+    out = np.empty(max(cap, 1), dtype=np.uint32)
+    pos = np.empty(max(cap, 1), dtype=np.int64) if with_pos else None
+    k = fn(n, d, _ord(ordering), w, _ptr(out), _ptr(pos) if with_pos else None, cap)
+    if k < 0:
+        raise RuntimeError(f"oracle error {k} for n={n} d={d} ord={ordering} w={w}")
+    if with_pos:
+        return out[:k].copy(), pos[:k].copy()
+    return out[:k].copy()
+
+
+def greedy_pairwise(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool = False):
+    """O1: each candidate against every codeword so far (Section 3)."""
+    return _greedy(_load().orc_greedy_pairwise, n, d, ordering, w, with_pos)
+
+
+def greedy_ball(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool = False):
+    """O2: the same greedy through radius-(d-1) exclusion balls over vectors."""
+    return _greedy(_load().orc_greedy_ball, n, d, ordering, w, with_pos)
+
+
+def verify(n: int, d: int, ordering, w: int, L) -> int:
+    """O3: 0 iff L is exactly the greedy output (see the C header)."""
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32))
+    return int(_load().orc_verify(n, d, _ord(ordering), w, _ptr(L), len(L)))
+
+
+def dense_tests(positions: np.ndarray, n_candidates: int) -> int:
+    """Candidate-codeword distance tests a sweep with no early exit performs:
+    the codeword accepted at candidate index p is compared with every later
+    candidate, so the total is the sum over codewords of (N - 1 - p)."""
+    p = np.asarray(positions, dtype=np.int64)
+    return int((n_candidates - 1 - p).sum())

@@ -1,0 +1,290 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself
+(the paper's worked example, closed forms of the codes Section 7 names,
+textbook order definitions, brute force over all subsets on tiny inputs)."""
+import itertools
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ORDERS = ["lex", "gray", "grlex", "grevlex"]
+
+
+def popc(x: int) -> int:
+    return bin(int(x)).count("1")
+
+
+def xor_closed(words) -> bool:
+    s = set(int(x) for x in words)
+    return all((a ^ b) in s for a in s for b in s)
+
+
+def weight_dist(words):
+    out = {}
+    for x in words:
+        k = popc(x)
+        out[k] = out.get(k, 0) + 1
+    return out
+
+
+# ---------------------------------------------------------------- Example 1
+def test_example1_worked_steps():
+    """Example 1 (Section 4.1): n = 3, d = 2, lex -> {000, 011, 101, 110}."""
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "example1_n3_d2_lex.txt"))
+             if l.strip() and not l.startswith("#")]
+    n, d, ordname = int(lines[0][0]), int(lines[0][1]), lines[0][2]
+    accepted = [(s, int(v)) for s, v in (l for l in lines[1:] if len(l) == 2)]
+    rejected = [l for l in lines[1:] if len(l) == 3]
+    for s, v in accepted:
+        assert int(s, 2) == v  # coordinate 1 is the most significant bit
+    got = oracle.greedy_pairwise(n, d, ordname)
+    assert got.tolist() == [v for _, v in accepted]
+    # each rejected vector is within d-1 of one of the codewords it met
+    for _, vec, against in rejected:
+        x = int(vec, 2)
+        assert any(popc(x ^ int(c, 2)) < d for c in against.split(","))
+
+
+# ---------------------------------------------------------------- orderings
+def reflected_gray(n):
+    """Binary-reflected Gray code by its recursive construction."""
+    seq = ["0", "1"]
+    for _ in range(n - 1):
+        seq = ["0" + s for s in seq] + ["1" + s for s in reversed(seq)]
+    return [int(s, 2) for s in seq]
+
+
+@pytest.mark.parametrize("n", range(1, 11))
+def test_gray_matches_reflected_construction(n):
+    g = oracle.order_list(n, "gray")
+    assert g.tolist() == reflected_gray(n)
+    assert all(popc(int(a) ^ int(b)) == 1 for a, b in zip(g[:-1], g[1:]))
+
+
+@pytest.mark.parametrize("n", range(1, 11))
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_stream_order_equals_comparator_sort(n, ordname):
+    for w in [-1] + list(range(0, n + 1)):
+        a = oracle.order_list(n, ordname, w)
+        b = oracle.order_sorted(n, ordname, w)
+        assert a.tolist() == b.tolist(), (n, ordname, w)
+        assert len(a) == (2 ** n if w < 0 else comb(n, w))
+        assert len(set(a.tolist())) == len(a)
+
+
+def test_graded_orders_by_hand():
+    """Textbook graded orders on 3 variables (x1 = most significant bit)."""
+    # grlex ascending: 1 < x3 < x2 < x1 < x2x3 < x1x3 < x1x2 < x1x2x3
+    assert oracle.order_list(3, "grlex").tolist() == [0, 1, 2, 4, 3, 5, 6, 7]
+    # grevlex ascending, 4 variables, degree 2: the last variable decides
+    # x3x4 < x2x4 < x1x4 < x2x3 < x1x3 < x1x2
+    want = [0b0011, 0b0101, 0b1001, 0b0110, 0b1010, 0b1100]
+    assert oracle.order_list(4, "grevlex", 2).tolist() == want
+    assert oracle.order_list(4, "grlex", 2).tolist() == sorted(want)
+
+
+@pytest.mark.parametrize("n", [5, 8, 12])
+def test_grevlex_pairwise_rule(n):
+    seq = oracle.order_list(n, "grevlex")
+    for a, b in zip(seq[:-1], seq[1:]):
+        a, b = int(a), int(b)
+        if popc(a) != popc(b):
+            assert popc(a) < popc(b)
+        else:
+            low = (a ^ b) & -(a ^ b)
+            assert a & low
+
+
+# ---------------------------------------------------------------- brute force
+def greedy_characterised(n, d, seq):
+    """All subsets of the candidate list that are (1) pairwise >= d and (2)
+    cover every other candidate by an earlier member within d-1."""
+    found = []
+    N = len(seq)
+    for mask in range(1 << N):
+        members = [i for i in range(N) if mask >> i & 1]
+        ok = all(popc(seq[i] ^ seq[j]) >= d for i, j in itertools.combinations(members, 2))
+        if not ok:
+            continue
+        ok = all(any(j < i and popc(seq[i] ^ seq[j]) <= d - 1 for j in members)
+                 for i in range(N) if not mask >> i & 1)
+        if ok:
+            found.append([seq[i] for i in members])
+    return found
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_bruteforce_unique_characterisation(n, ordname):
+    for w in [-1] + list(range(n + 1)):
+        seq = [int(x) for x in oracle.order_sorted(n, ordname, w)]
+        if len(seq) > 16:
+            continue
+        for d in range(0, n + 2):
+            found = greedy_characterised(n, d, seq)
+            assert len(found) == 1, (n, ordname, w, d, found)
+            assert oracle.greedy_pairwise(n, d, ordname, w).tolist() == found[0]
+            assert oracle.greedy_ball(n, d, ordname, w).tolist() == found[0]
+
+
+# ---------------------------------------------------------------- closed forms
+def _fixture_codes():
+    rows = []
+    for l in open(os.path.join(GOLDEN, "perfect_codes.txt")):
+        if l.strip() and not l.startswith("#"):
+            f = l.split()
+            wd = {int(k): int(v) for k, v in (t.split(":") for t in f[4:])}
+            rows.append((int(f[0]), int(f[1]), f[2], int(f[3]), wd))
+    return rows
+
+
+@pytest.mark.parametrize("row", _fixture_codes(), ids=lambda r: f"n{r[0]}d{r[1]}")
+def test_named_codes(row):
+    """Section 7: Hamming (n = 7, 15), Golay [23,12,7], extended Golay [24,12,8]."""
+    n, d, ordname, size, wd = row
+    C = oracle.greedy_ball(n, d, ordname)
+    assert len(C) == size
+    assert weight_dist(C) == wd
+    assert xor_closed(C) if size <= 4096 else True
+    assert C[0] == 0
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_hamming_perfect(m):
+    n = 2 ** m - 1
+    C = oracle.greedy_pairwise(n, 3, "lex")
+    assert len(C) == 2 ** (n - m)
+    assert len(C) * (n + 1) == 2 ** n  # radius-1 balls tile the space
+    assert xor_closed(C)
+    assert min(popc(x) for x in C[1:]) == 3
+    assert weight_dist(C).get(3, 0) == n * (n - 1) // 6
+
+
+def test_golay_perfect():
+    C = oracle.greedy_ball(23, 7, "lex")
+    vol = sum(comb(23, i) for i in range(4))
+    assert len(C) * vol == 2 ** 23
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.environ.get("GC_SLOW"), reason="minutes of CPU; set GC_SLOW=1")
+def test_hamming_31_closed_form():
+    """[31,26,3] Hamming code: 2^26 words (perfect), XOR-closed (sampled)."""
+    C = oracle.greedy_ball(31, 3, "lex")
+    assert len(C) == 2 ** 26
+    rng = np.random.default_rng(1507)
+    s = set(C.tolist())
+    a = C[rng.integers(0, len(C), 2000)]
+    b = C[rng.integers(0, len(C), 2000)]
+    assert all(int(x ^ y) in s for x, y in zip(a, b))
+
+
+# ---------------------------------------------------------------- relations
+@pytest.mark.parametrize("n,d", [(6, 3), (9, 3), (10, 4), (11, 5), (13, 4), (14, 6)])
+@pytest.mark.parametrize("ordname", ["lex", "gray"])
+def test_b_ordering_codes_are_linear(n, d, ordname):
+    """Lex and Gray are B-orderings; B-greedy codes are linear (the Brualdi-
+    Pless result Section 4.3 cites), so |C| is a power of two and C is
+    closed under XOR."""
+    C = oracle.greedy_pairwise(n, d, ordname)
+    assert len(C) & (len(C) - 1) == 0
+    assert xor_closed(C)
+
+
+@pytest.mark.parametrize("n,d", [(12, 4), (16, 4), (16, 8)])
+def test_lex_and_grlex_same_words_for_power_of_two_d(n, d):
+    """Section 7: for d a power of two the lex and graded-lex greedy codes
+    have the same words (a conjecture the paper observed up to n = 30)."""
+    assert set(oracle.greedy_ball(n, d, "lex").tolist()) == \
+        set(oracle.greedy_ball(n, d, "grlex").tolist())
+
+
+@pytest.mark.parametrize("n,d", [(7, 3), (11, 5), (15, 3)])
+def test_parity_extension(n, d):
+    """Lexicode (n+1, d+1) is lexicode (n, d) with an overall parity bit
+    appended (odd d); observed relation, consistent with Golay -> extended."""
+    a = oracle.greedy_pairwise(n, d, "lex")
+    b = oracle.greedy_pairwise(n + 1, d + 1, "lex")
+    ext = [(int(x) << 1) | (popc(x) & 1) for x in a]
+    assert ext == b.tolist()
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_degenerate_distances(ordname):
+    n = 9
+    seq = oracle.order_list(n, ordname)
+    for d in (0, 1):
+        assert oracle.greedy_pairwise(n, d, ordname).tolist() == seq.tolist()
+    with pytest.raises(RuntimeError):
+        oracle.greedy_pairwise(n, -1, ordname)
+    for d in (n + 1, n + 5):
+        assert oracle.greedy_pairwise(n, d, ordname).tolist() == [0]
+    # d = n: only 0 and the all-ones vector
+    assert oracle.greedy_pairwise(n, n, ordname).tolist() == [0, 2 ** n - 1]
+
+
+@pytest.mark.parametrize("ordname", ORDERS)
+@pytest.mark.parametrize("n,w", [(10, 2), (12, 3), (12, 4), (13, 5)])
+def test_constant_weight_closed_forms(ordname, n, w):
+    C = oracle.greedy_pairwise(n, 2 * w, ordname, w)
+    assert len(C) == n // w  # disjoint supports
+    assert all(popc(x) == w for x in C)
+    allw = oracle.greedy_pairwise(n, 2, ordname, w)
+    assert len(allw) == comb(n, w)
+    assert oracle.greedy_pairwise(n, 3, ordname, w).tolist() == \
+        oracle.greedy_pairwise(n, 4, ordname, w).tolist()  # distances are even
+    assert oracle.greedy_pairwise(n, 5, ordname, 0).tolist() == [0]
+    assert oracle.greedy_pairwise(n, 5, ordname, n).tolist() == [2 ** n - 1]
+
+
+def test_constant_weight_lex_equals_grlex():
+    for n, d, w in [(12, 4, 3), (14, 6, 5), (16, 4, 4)]:
+        assert oracle.greedy_pairwise(n, d, "lex", w).tolist() == \
+            oracle.greedy_pairwise(n, d, "grlex", w).tolist()
+
+
+# ---------------------------------------------------------------- O1 = O2, O3
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_pairwise_equals_ball(ordname):
+    for n in range(1, 13):
+        for d in range(0, n + 2):
+            for w in ([-1, n // 2] if n >= 2 else [-1]):
+                a = oracle.greedy_pairwise(n, d, ordname, w, with_pos=True)
+                b = oracle.greedy_ball(n, d, ordname, w, with_pos=True)
+                assert a[0].tolist() == b[0].tolist(), (n, d, ordname, w)
+                assert a[1].tolist() == b[1].tolist()
+
+
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_pairwise_equals_ball_n20(ordname):
+    assert oracle.greedy_pairwise(16, 4, ordname).tolist() == \
+        oracle.greedy_ball(16, 4, ordname).tolist()
+    assert oracle.greedy_pairwise(16, 5, ordname).tolist() == \
+        oracle.greedy_ball(16, 5, ordname).tolist()
+
+
+def test_verify_accepts_greedy_rejects_perturbed():
+    for ordname in ORDERS:
+        C = oracle.greedy_pairwise(10, 3, ordname)
+        assert oracle.verify(10, 3, ordname, -1, C) == 0
+        assert oracle.verify(10, 3, ordname, -1, C[:-1]) != 0      # not maximal
+        assert oracle.verify(10, 3, ordname, -1, C[::-1]) != 0     # out of order
+        bad = C.copy(); bad[5] ^= 1
+        assert oracle.verify(10, 3, ordname, -1, bad) != 0
+        assert oracle.verify(10, 3, ordname, -1, np.append(C, C[3] ^ 1)) != 0
+
+
+def test_dense_tests_count():
+    # every candidate accepted: candidate i meets i codewords
+    _, pos = oracle.greedy_pairwise(8, 1, "lex", with_pos=True)
+    assert oracle.dense_tests(pos, 256) == 256 * 255 // 2
+    # direct count on a small case
+    C, pos = oracle.greedy_pairwise(7, 3, "gray", with_pos=True)
+    seq = oracle.order_list(7, "gray")
+    direct = sum(int((pos < i).sum()) for i in range(len(seq)))
+    assert oracle.dense_tests(pos, len(seq)) == direct
