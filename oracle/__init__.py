@@ -17,6 +17,10 @@ Parity status of each function (the pins are in ``tests/test_oracle.py``):
   greedy_ball (O2)           pinned (equal to O1 wherever O1 runs; Hamming
                              [31,26,3] closed form)
   verify (O3)                pinned (brute force: accepts exactly one subset)
+  block_test / resolve /     pinned (brute force on small lists; resolve over the
+  ball_mark / scan           whole order equals O1; the greedy code's balls
+                             cover every candidate; scan of an empty map is the
+                             order itself)
 """
 from __future__ import annotations
 
@@ -70,6 +74,15 @@ def _load():
             lib.orc_verify.argtypes = [i32, i32, i32, i32, u32p, i64]
             lib.orc_distance.restype = i32
             lib.orc_distance.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            lib.orc_block_test.restype = None
+            lib.orc_block_test.argtypes = [i32, u32p, i64, u32p, i64, u32p]
+            lib.orc_resolve.restype = i64
+            lib.orc_resolve.argtypes = [i32, u32p, i64, i64p]
+            lib.orc_ball_mark.restype = i32
+            lib.orc_ball_mark.argtypes = [i32, i32, u32p, i64, u32p]
+            lib.orc_scan.restype = i64
+            lib.orc_scan.argtypes = [i32, i32, i32, u32p, ctypes.c_uint64, ctypes.c_uint64,
+                                     u32p, i64]
             _lib = lib
     return _lib
 
@@ -133,6 +146,44 @@ def verify(n: int, d: int, ordering, w: int, L) -> int:
     """O3: 0 iff L is exactly the greedy output (see the C header)."""
     L = np.ascontiguousarray(np.asarray(L, dtype=np.uint32))
     return int(_load().orc_verify(n, d, _ord(ordering), w, _ptr(L), len(L)))
+
+
+def block_test(d: int, cand, code) -> np.ndarray:
+    """alive[i] = 1 iff cand[i] is at distance >= d from every codeword."""
+    c = np.ascontiguousarray(np.asarray(cand, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(code, dtype=np.uint32))
+    alive = np.empty(max(len(c), 1), dtype=np.uint8)
+    _load().orc_block_test(d, _ptr(c), len(c), _ptr(k), len(k), _ptr(alive))
+    return alive[:len(c)].copy()
+
+
+def resolve(d: int, cand) -> np.ndarray:
+    """List indices the greedy accepts when the list is walked in order."""
+    c = np.ascontiguousarray(np.asarray(cand, dtype=np.uint32))
+    idx = np.empty(max(len(c), 1), dtype=np.int64)
+    k = _load().orc_resolve(d, _ptr(c), len(c), _ptr(idx))
+    return idx[:k].copy()
+
+
+def ball_mark(n: int, d: int, code, bitmap=None) -> np.ndarray:
+    """OR the radius-(d-1) balls of the codewords into a 2^n-bit map."""
+    k = np.ascontiguousarray(np.asarray(code, dtype=np.uint32))
+    if bitmap is None:
+        bitmap = np.zeros(max(((1 << n) + 31) // 32, 1), dtype=np.uint32)
+    rc = _load().orc_ball_mark(n, d, _ptr(k), len(k), _ptr(bitmap))
+    if rc != 0:
+        raise RuntimeError(f"oracle ball_mark error {rc}")
+    return bitmap
+
+
+def scan(n: int, ordering, w: int, bitmap, rank0: int, count: int):
+    """Vectors of ranks [rank0, rank0+count) whose bit is clear, in order."""
+    b = np.ascontiguousarray(np.asarray(bitmap, dtype=np.uint32))
+    out = np.empty(max(count, 1), dtype=np.uint32)
+    k = _load().orc_scan(n, _ord(ordering), w, _ptr(b), rank0, count, _ptr(out), count)
+    if k < 0:
+        raise RuntimeError(f"oracle scan error {k}")
+    return out[:k].copy()
 
 
 def dense_tests(positions: np.ndarray, n_candidates: int) -> int:

@@ -327,3 +327,82 @@ int orc_verify(int n, int d, int ord, int w, const uint32_t *L, int64_t len) {
     }
     return i == len ? 0 : 1;
 }
+
+/* ---- the steps of the sweep, one at a time ------------------------------ */
+/* Block distance test (Sections 4.1, 5.2): alive[i] = 1 iff cand[i] is at
+ * distance >= d from every code[j]. */
+void orc_block_test(int d, const uint32_t *cand, int64_t nc, const uint32_t *code,
+                    int64_t nk, uint8_t *alive) {
+    for (int64_t i = 0; i < nc; ++i) {
+        int ok = 1;
+        for (int64_t j = 0; j < nk; ++j)
+            if (orc_distance(cand[i], code[j]) < d) { ok = 0; break; }
+        alive[i] = (uint8_t)ok;
+    }
+}
+
+/* In-order resolve: the greedy of Section 3 applied to a given list (the list
+ * takes the place of the ordered space).  Writes the list indices of the
+ * accepted entries; returns how many. */
+int64_t orc_resolve(int d, const uint32_t *cand, int64_t nc, int64_t *acc_idx) {
+    int64_t na = 0;
+    for (int64_t i = 0; i < nc; ++i) {
+        int ok = 1;
+        for (int64_t j = 0; j < na; ++j)
+            if (orc_distance(cand[i], cand[acc_idx[j]]) < d) { ok = 0; break; }
+        if (ok) acc_idx[na++] = i;
+    }
+    return na;
+}
+
+/* Exclusion-ball marking: set bit (c ^ e) for every codeword c and every e of
+ * weight <= d-1; bit v of the map is word v/32, bit v%32. */
+int orc_ball_mark(int n, int d, const uint32_t *code, int64_t nk, uint32_t *bitmap) {
+    if (n < 1 || n > 32) return ORC_EINVAL;
+    uint64_t blen = 0;
+    uint32_t *ball = ball_list(n, d - 1, &blen);
+    if (!ball) return ORC_ENOMEM;
+    if (d <= 0) blen = 0;
+    for (int64_t i = 0; i < nk; ++i)
+        for (uint64_t j = 0; j < blen; ++j) {
+            uint32_t y = code[i] ^ ball[j];
+            bitmap[y >> 5] |= 1u << (y & 31);
+        }
+    free(ball);
+    return 0;
+}
+
+/* Find-unmarked scan over ranks [rank0, rank0 + count) of the rank space:
+ * 2^n ranks with no weight or for GRAY (Gray ranks of the wrong weight are
+ * skipped), else the C(n, w) ranks of the weight-w class in order.  Writes the
+ * vectors whose bit is clear, in rank order; returns how many were clear. */
+int64_t orc_scan(int n, int ord, int w, const uint32_t *bitmap, uint64_t rank0,
+                 uint64_t count, uint32_t *out, int64_t cap) {
+    if (!valid_args(n, ord, w)) return ORC_EINVAL;
+    int64_t found = 0;
+    uint64_t r = 0;
+    if (ord == ORC_GRAY || w < 0) {
+        /* walk the full order with no weight, then apply the filter */
+        orc_iter it; iter_init(&it, n, ord, -1);
+        uint32_t x;
+        while (r < rank0 + count && iter_next(&it, &x)) {
+            if (r >= rank0 && (w < 0 || orc_popcount(x) == w) &&
+                !(bitmap[x >> 5] >> (x & 31) & 1)) {
+                if (found < cap) out[found] = x;
+                ++found;
+            }
+            ++r;
+        }
+    } else {
+        orc_iter it; iter_init(&it, n, ord, w);
+        uint32_t x;
+        while (r < rank0 + count && iter_next(&it, &x)) {
+            if (r >= rank0 && !(bitmap[x >> 5] >> (x & 31) & 1)) {
+                if (found < cap) out[found] = x;
+                ++found;
+            }
+            ++r;
+        }
+    }
+    return found;
+}

@@ -288,3 +288,61 @@ def test_dense_tests_count():
     seq = oracle.order_list(7, "gray")
     direct = sum(int((pos < i).sum()) for i in range(len(seq)))
     assert oracle.dense_tests(pos, len(seq)) == direct
+
+
+# ---------------------------------------------------------------- step forms
+def test_step_block_test_bruteforce():
+    rng = np.random.default_rng(7)
+    for n, d in [(6, 2), (9, 3), (12, 5), (20, 6)]:
+        cand = rng.integers(0, 1 << n, 300, dtype=np.uint64).astype(np.uint32)
+        code = rng.integers(0, 1 << n, 40, dtype=np.uint64).astype(np.uint32)
+        want = [int(all(popc(int(x) ^ int(c)) >= d for c in code)) for x in cand]
+        assert oracle.block_test(d, cand, code).tolist() == want
+    assert oracle.block_test(3, [5], []).tolist() == [1]
+
+
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_step_resolve_over_whole_order_is_greedy(ordname):
+    for n, d, w in [(9, 3, -1), (11, 4, -1), (12, 4, 5), (8, 5, -1)]:
+        seq = oracle.order_list(n, ordname, w)
+        idx = oracle.resolve(d, seq)
+        assert seq[idx].tolist() == oracle.greedy_pairwise(n, d, ordname, w).tolist()
+
+
+def test_step_ball_mark_covers_space_and_matches_bruteforce():
+    for n, d in [(7, 3), (10, 4), (12, 5)]:
+        C = oracle.greedy_pairwise(n, d, "lex")
+        bm = oracle.ball_mark(n, d, C)
+        # maximality of the greedy code: every vector within d-1 of a codeword
+        assert all((int(bm[v >> 5]) >> (v & 31)) & 1 for v in range(1 << n))
+    rng = np.random.default_rng(3)
+    code = rng.integers(0, 1 << 9, 5, dtype=np.uint64).astype(np.uint32)
+    bm = oracle.ball_mark(9, 3, code)
+    for v in range(1 << 9):
+        want = any(popc(v ^ int(c)) <= 2 for c in code)
+        assert bool((int(bm[v >> 5]) >> (v & 31)) & 1) == want
+
+
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_step_scan(ordname):
+    n = 9
+    empty = np.zeros(16, dtype=np.uint32)
+    assert oracle.scan(n, ordname, -1, empty, 0, 512).tolist() == \
+        oracle.order_list(n, ordname).tolist()
+    assert oracle.scan(n, ordname, -1, empty, 100, 50).tolist() == \
+        oracle.order_list(n, ordname)[100:150].tolist()
+    full = np.full(16, 0xFFFFFFFF, dtype=np.uint32)
+    assert len(oracle.scan(n, ordname, -1, full, 0, 512)) == 0
+    rng = np.random.default_rng(11)
+    bm = rng.integers(0, 1 << 32, 16, dtype=np.uint64).astype(np.uint32)
+    seq = oracle.order_list(n, ordname)
+    want = [int(x) for x in seq[37:400] if not (int(bm[x >> 5]) >> (int(x) & 31)) & 1]
+    assert oracle.scan(n, ordname, -1, bm, 37, 363).tolist() == want
+    # weight-restricted rank spaces
+    w = 4
+    if ordname == "gray":
+        sub = [int(x) for x in seq if popc(x) == w]
+    else:
+        sub = oracle.order_list(n, ordname, w).tolist()
+    assert oracle.scan(n, ordname, w, empty, 0, len(seq) if ordname == "gray" else comb(n, w)) \
+        .tolist() == sub
