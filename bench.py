@@ -1,0 +1,295 @@
+"""Benchmark of the ordered greedy code sweep on one GB300 (or N replicas).
+
+Workload (one "step"): the five codes n=24, d=8 lex (extended Golay) and
+n=20, d=4 in lex, Gray, graded-lex and graded-reverse-lex order, each one
+whole sweep over all 2^n candidates.  Metric: candidate-codeword distance
+tests per second, counted as dense-equivalent tests (for each candidate, the
+number of codewords accepted before it -- the tests a sweep without early
+exit performs, the paper's naive kernel) divided by the device time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs the same
+workload as an independent replica (the sweep of one code does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = [(24, 8, "lex"), (20, 4, "lex"), (20, 4, "gray"), (20, 4, "grlex"), (20, 4, "grevlex")]
+WORKLOAD_NAME = "n=24 d=8 lex + n=20 d=4 x {lex, gray, grlex, grevlex}"
+METRIC = "candidate-codeword distance tests/s (dense-equivalent)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args):
+    """The CPU oracle, single-threaded, as it stands: each step is one code of
+    the workload (rotating), so K steps cover a bounded sample of it."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    dense = 0
+    seconds = 0.0
+    sample = []
+    for i in range(args.warmup + args.steps):
+        n, d, o = WORKLOAD[i % len(WORKLOAD)]
+        t = time.perf_counter()
+        C, pos = oracle.greedy_pairwise(n, d, o, with_pos=True)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            dense += oracle.dense_tests(pos, 1 << n)
+            seconds += dt
+            sample.append(f"n={n} d={d} {o}")
+    value = dense / seconds
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "tests/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * seconds / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (fully determined by n, d, order)",
+        "config": {"workload": WORKLOAD_NAME, "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": "tests/s", "cores": 1, "kind": "oracle",
+                         "sample": "; ".join(sample) + " (pairwise oracle, one code per step)",
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "tests/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+def cpu_baseline_sample():
+    import oracle
+    oracle.build()
+    dense, secs, parts = 0, 0.0, []
+    for n, d, o in [(24, 8, "lex"), (20, 4, "lex")]:
+        t = time.perf_counter()
+        C, pos = oracle.greedy_pairwise(n, d, o, with_pos=True)
+        secs += time.perf_counter() - t
+        dense += oracle.dense_tests(pos, 1 << n)
+        parts.append(f"n={n} d={d} {o}")
+    return {"value": dense / secs, "unit": "tests/s", "cores": 1, "kind": "oracle",
+            "sample": " + ".join(parts) + " (pairwise oracle, whole sweeps, "
+                      f"{secs:.1f} s)", "cpu": cpu_model()}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1507_05398_gb300 as G
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # resident buffers: outputs, stats and workspaces for the five codes
+    jobs = []
+    for n, d, o in WORKLOAD:
+        pl = G.plan(n, d, o)
+        cap = G.capacity_bound(n, d)
+        ws_bytes = G.workspace_size(n, d, o)
+        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+        base = (-ws.data_ptr()) % 256
+        jobs.append({"n": n, "d": d, "o": o, "strategy": pl.strategy,
+                     "out": torch.empty(cap, dtype=torch.int32, device=dev),
+                     "stats": torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=dev),
+                     "ws": ws[base:base + ws_bytes]})
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one_step(events=None):
+        for k, j in enumerate(jobs):
+            if events is not None:
+                events[k][0].record(stream)
+            G.generate_async(j["n"], j["d"], j["o"], out=j["out"], stats=j["stats"],
+                             workspace=j["ws"], stream=stream)
+            if events is not None:
+                events[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    stats = [G.stats_from(j["stats"]) for j in jobs]
+    for s in stats:
+        if s.status != 0:
+            raise RuntimeError(f"sweep failed: {s.as_dict()}")
+    dense = sum(s.dense_tests for s in stats)
+    executed = sum(s.executed_tests for s in stats)
+    launches_per_step = sum(2 if j["strategy"] == G.STRATEGY_BITMAP else 1 for j in jobs)
+
+    # timed region: K steps, L2 flushed before each, CUDA events per code
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+           for _ in jobs] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            one_step(ev[s])
+        torch.cuda.synchronize()
+    per_code_ms = [[ev[s][k][0].elapsed_time(ev[s][k][1]) for s in range(args.steps)]
+                   for k in range(len(jobs))]
+    step_ms = [sum(per_code_ms[k][s] for k in range(len(jobs))) for s in range(args.steps)]
+    mean_step_ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([mean_step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_step_ms = float(t.item())
+    value = world * dense / (mean_step_ms * 1e-3)
+
+    # end to end through the public host API (allocation, sweep, copy back)
+    e2e_times, d2h = [], 0
+    for s in range(args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        words = 0
+        for j in jobs:
+            words += len(G.generate_host(j["n"], j["d"], j["o"]))
+        e2e_times.append(time.perf_counter() - t)
+        d2h = words * 4 + ctypes.sizeof(G.Stats) * len(jobs)
+    e2e_value = world * dense / statistics.mean(e2e_times)
+
+    # roofline of the sweep kernel: executed tests per second against the
+    # measured register-operand test rate of this GPU
+    peak, _ = G.probe_test_rate()
+    sweep_s = mean_step_ms * 1e-3
+    achieved = executed / sweep_s
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = cpu_baseline_sample() if world == 1 and not args.no_cpu else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (fully determined by n, d, order)",
+        "config": {"workload": WORKLOAD_NAME, "codes_per_step": len(jobs),
+                   "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "strategies": {f"n={j['n']} d={j['d']} {j['o']}":
+                                  ("bitmap" if j["strategy"] == 2 else "distance") for j in jobs}},
+        "per_code_ms": {f"n={j['n']} d={j['d']} {j['o']}": statistics.mean(per_code_ms[k])
+                        for k, j in enumerate(jobs)},
+        "dense_tests_per_step": dense, "executed_tests_per_step": executed,
+        "executed_tests_per_s": executed / sweep_s,
+        "e2e": {"value": e2e_value, "unit": "tests/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(e2e_times)},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "tests/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "gc::sweep_kernel",
+                     "peak_source": "gc_probe_test_rate (register-operand XOR+popcount+compare, "
+                                    "measured in this run)"},
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * gc.h -- C ABI of libgc, a GB300 (sm_103a) library for the ordered greedy
+ * construction of binary codes.
+ *
+ * The method (Section 3, "Greedy Algorithms and Different Orderings"): order
+ * the vectors of F_2^n, optionally only those of weight w; walk the order from
+ * its first vector (the zero vector when no weight is given) and append a
+ * vector to the code C iff its Hamming distance to every codeword already in C
+ * is at least d.  Hamming distance is popcount(x XOR c) (Section 5.2).  The
+ * four orderings are those Section 4.2 names.
+ *
+ * Conventions shared by every entry point:
+ *  - A length-n vector is the low n bits of a uint32_t, coordinate 1 in the
+ *    most significant of those bits ("011" is 3).  1 <= n <= 32.
+ *  - Orderings (the paper names them but defines none; these are the readings):
+ *      GC_ORDER_LEX      ascending integer (Example 1 of Section 4.1).
+ *      GC_ORDER_GRAY     binary-reflected Gray code: rank r -> r ^ (r >> 1).
+ *      GC_ORDER_GRLEX    weight ascending, then ascending integer.
+ *      GC_ORDER_GREVLEX  weight ascending; within a weight, a precedes b iff
+ *                        a has the 1 at the lowest bit where a and b differ
+ *                        (textbook graded reverse lexicographic order).
+ *  - Constant weight: weight_or_none in [0, n] keeps only weight-w vectors, in
+ *    the same relative order; GC_NO_WEIGHT (-1) keeps all 2^n vectors.
+ *  - "Rank space" of a problem: 2^n ranks when no weight is given or the
+ *    order is GRAY (Gray ranks of the wrong weight are skipped); C(n, w)
+ *    ranks for LEX, GRLEX and GREVLEX with a weight (LEX and GRLEX restricted
+ *    to one weight are the same sequence).
+ *  - Return value: GC_OK (0) or a positive GC_ERR_* code; no exception or
+ *    abort crosses the ABI.  gc_strerror() names the code; gc_last_error()
+ *    returns a one-line message about the most recent failure on the calling
+ *    thread.
+ *  - Pointers marked "device" must be device memory of the current CUDA
+ *    device (or managed memory); "host" pointers are ordinary host memory.
+ *    Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes.
+ *  - Asynchronous entry points take a cudaStream_t as void*; NULL is the
+ *    legacy default stream.  They return after launching; errors detected on
+ *    the device (a bounded wait that expired, an overflow) are reported in the
+ *    gc_stats block they fill, readable once the stream has completed.
+ */
+#ifndef GC_H_
+#define GC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GC_ORDER_LEX = 0,
+    GC_ORDER_GRAY = 1,
+    GC_ORDER_GRLEX = 2,
+    GC_ORDER_GREVLEX = 3
+} gc_ordering;
+
+#define GC_NO_WEIGHT (-1)
+
+enum {
+    GC_OK = 0,
+    GC_ERR_INVALID = 1,     /* argument out of range */
+    GC_ERR_CAPACITY = 2,    /* output buffer too small; nothing was written
+                               past the capacity, *inout_count = required */
+    GC_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    GC_ERR_OOM = 4,         /* device or host allocation failed */
+    GC_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    GC_ERR_UNSUPPORTED = 6, /* valid request this build does not handle */
+    GC_ERR_INTERNAL = 7     /* an internal consistency check failed */
+};
+
+/* Sweep strategy.  AUTO lets gc_plan() choose. */
+typedef enum {
+    GC_STRATEGY_AUTO = 0,
+    GC_STRATEGY_DISTANCE = 1, /* test each candidate against the code */
+    GC_STRATEGY_BITMAP = 2    /* exclusion bitmap of radius-(d-1) balls */
+} gc_strategy;
+
+/* One problem instance. */
+typedef struct {
+    int n;              /* code length, 1..32 */
+    int d;              /* minimum distance, >= 0 (d <= 1 accepts all) */
+    int ordering;       /* gc_ordering */
+    int weight;         /* GC_NO_WEIGHT or 0..n */
+} gc_problem;
+
+/* Launch plan chosen by gc_plan() (or given by the caller). */
+typedef struct {
+    int strategy;          /* gc_strategy, never AUTO after gc_plan() */
+    int grid;              /* CTAs of the persistent sweep (0 = all SMs) */
+    int block;             /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t window_min;   /* smallest window of ranks tested per step */
+    uint32_t window_max;   /* largest window */
+    uint32_t survivor_target; /* window sizing aims at this many survivors */
+} gc_plan_t;
+
+/* Counters filled by the sweep (device-side writes, read after sync). */
+typedef struct {
+    uint64_t codewords;        /* |C| (the true size even past capacity) */
+    uint64_t candidates;       /* candidates swept (rank-space size) */
+    uint64_t dense_tests;      /* sum over candidates of |C before it| */
+    uint64_t executed_tests;   /* distance tests the kernels executed */
+    uint64_t marks;            /* bitmap words OR-ed by ball marking */
+    uint64_t windows;          /* sequential window steps */
+    uint64_t survivors;        /* candidates that reached the resolver */
+    int32_t status;            /* GC_OK or GC_ERR_TIMEOUT / _INTERNAL */
+    int32_t strategy;          /* strategy that ran */
+} gc_stats;
+
+/* ---- information ------------------------------------------------------ */
+
+/* Static string naming an error code. */
+const char *gc_strerror(int err);
+
+/* One-line description of the last failure on this thread ("" if none). */
+const char *gc_last_error(void);
+
+/* Rank-space size of a problem (see "Rank space" above), 0 if invalid. */
+uint64_t gc_candidate_count(int n, int weight_or_none, int ordering);
+
+/* An upper bound on |C| that is always safe as an output capacity:
+ * min(number of weight-admissible candidates, sphere-packing bound
+ * floor(2^n / V(n, floor((d-1)/2)))) -- the radius-floor((d-1)/2) balls
+ * around codewords are disjoint.  Returns 0 for invalid arguments. */
+uint64_t gc_capacity_bound(int n, int d, int weight_or_none);
+
+/* Choose a strategy and launch shape for a problem on the current device.
+ * The cost model compares the estimated number of distance tests of the
+ * distance strategy with the number of bitmap words the ball marking of the
+ * bitmap strategy would OR (the paper's own observation, Section 6, is that
+ * the best parallel form depends on how d compares with n).  Returns GC_OK
+ * or GC_ERR_INVALID. */
+int gc_plan(const gc_problem *prob, gc_plan_t *out_plan);
+
+/* ---- the whole sweep ---------------------------------------------------- */
+
+/* Device bytes of scratch gc_generate_async() needs for this problem and
+ * plan (plan NULL = gc_plan()'s choice).  0 on invalid arguments. */
+size_t gc_workspace_size(const gc_problem *prob, const gc_plan_t *plan);
+
+/* Generate the greedy code (Section 3) on the current device, synchronously.
+ *   out_codewords  host or device buffer of *inout_count uint32_t words;
+ *                  receives the code in acceptance (= rank) order.
+ *   inout_count    in: capacity in words; out: |C|.
+ * Returns GC_ERR_CAPACITY (with *inout_count = |C| and the first capacity
+ * words written) if the buffer is too small.  Allocates its scratch with
+ * cudaMallocAsync on an internal stream and frees it before returning. */
+int gc_generate(int n, int d, int ordering, int weight_or_none,
+                uint32_t *out_codewords, uint64_t *inout_count);
+
+/* Stream-ordered form.  All pointers are device pointers:
+ *   d_out        capacity words for the code (acceptance order);
+ *   d_stats      one gc_stats block, overwritten;
+ *   workspace    >= gc_workspace_size() bytes, 256-byte aligned, owned by
+ *                the caller and not touched after the stream passes this
+ *                call;
+ *   plan         NULL = gc_plan()'s choice.
+ * The code size is d_stats->codewords; words past capacity are not written.
+ * Returns GC_OK after a successful launch. */
+int gc_generate_async(const gc_problem *prob, const gc_plan_t *plan,
+                      uint32_t *d_out, uint64_t capacity, gc_stats *d_stats,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- the steps of the sweep, callable one at a time (for tests and for
+ *      callers composing their own pipeline) ------------------------------ */
+
+/* Step 1, ordering (Section 4.2): d_vectors[i] = the candidate of rank
+ * rank0 + i, for i < count, in the problem's rank space.  For GRAY with a
+ * weight the ranks index the full 2^n Gray sequence and the weight is not
+ * applied here (the sweep skips vectors of the wrong weight).  Device
+ * pointer; rank0 + count must not exceed the rank-space size
+ * (GC_ERR_INVALID otherwise). */
+int gc_unrank(int n, int ordering, int weight_or_none, uint64_t rank0,
+              uint64_t count, uint32_t *d_vectors, void *stream);
+
+/* Inverse of gc_unrank without a weight: d_ranks[i] = rank of d_vectors[i]
+ * in the full 2^n order (uint64 because 2^32 ranks exist at n = 32). */
+int gc_rank(int n, int ordering, const uint32_t *d_vectors, uint64_t count,
+            uint64_t *d_ranks, void *stream);
+
+/* Step 2, block distance test (Sections 4.1, 5.2): d_alive[i] = 1 iff
+ * popcount(cand[i] ^ code[j]) >= d for every j < ncode, else 0.  Candidates
+ * are tested in tiles against the code staged through shared memory, most
+ * recent codeword first, with warp-wide early exit.  Device pointers. */
+int gc_block_test(int d, const uint32_t *d_cand, uint64_t ncand,
+                  const uint32_t *d_code, uint64_t ncode, uint8_t *d_alive,
+                  void *stream);
+
+/* Step 3, in-order resolve (Section 3 restricted to a list): given
+ * candidates already known to clear every earlier codeword, accept them in
+ * list order exactly as the serial sweep would: d_accepted[k] = list index of
+ * the k-th accepted candidate, *d_count = number accepted.  ncand <= 65536.
+ * Device pointers. */
+int gc_resolve(int d, const uint32_t *d_cand, uint32_t ncand,
+               uint32_t *d_accepted, uint32_t *d_count, void *stream);
+
+/* Step 4, exclusion-ball marking: for every codeword c and every e of weight
+ * <= d-1, set bit (c ^ e) of the vector-indexed bitmap d_bitmap (2^n bits,
+ * word i holds vectors 32i..32i+31, bit b = vector 32i+b).  Device pointers;
+ * the bitmap is OR-ed into, not cleared. */
+int gc_bitmap_mark(int n, int d, const uint32_t *d_code, uint64_t ncode,
+                   uint32_t *d_bitmap, void *stream);
+
+/* Step 5, find-unmarked scan: walk ranks [rank0, rank0 + count) of the
+ * problem's rank space in order and write, in rank order, the vectors whose
+ * bitmap bit is clear to d_out (capacity words); *d_found = how many were
+ * clear (may exceed capacity; only capacity are written).  Device pointers. */
+int gc_bitmap_scan(int n, int ordering, int weight_or_none,
+                   const uint32_t *d_bitmap, uint64_t rank0, uint64_t count,
+                   uint32_t *d_out, uint64_t capacity, uint64_t *d_found,
+                   void *stream);
+
+/* ---- diagnostics ------------------------------------------------------ */
+
+/* Measures, on the current device, how many candidate-codeword distance
+ * tests per second the SMs sustain when operands sit in registers (XOR,
+ * popcount, compare): the arithmetic ceiling of the distance test (Section
+ * 5.2 reduces each test to one XOR and one population count).  Runs two
+ * short kernels and synchronises.  *sm_clock_hz_hint receives the device's
+ * reported SM clock (may be NULL). */
+int gc_probe_test_rate(double *tests_per_second, double *sm_clock_hz_hint);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H_ */

@@ -1,0 +1,345 @@
+// gc_capi.cu -- the extern "C" entry points of libgc: argument checks,
+// planning, workspace layout, allocation for the synchronous call, and the
+// launches.  No exception crosses the ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "gc_internal.h"
+
+namespace gc {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+uint64_t binom64(int n, int k) {
+    if (k < 0 || n < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+    return r;
+}
+
+static uint64_t ball_volume(int n, int r) {
+    uint64_t v = 0;
+    for (int k = 0; k <= r && k <= n; ++k) v += binom64(n, k);
+    return v;
+}
+
+bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why) {
+    if (n < 1 || n > 32) { *why = "n must be in [1, 32]"; return false; }
+    if (d < 0) { *why = "d must be >= 0"; return false; }
+    if (ord < GC_ORDER_LEX || ord > GC_ORDER_GREVLEX) { *why = "unknown ordering"; return false; }
+    if (w < -1 || w > n) { *why = "weight must be -1 or in [0, n]"; return false; }
+    p->n = n;
+    p->d = d;
+    p->ord = ord;
+    p->w = w;
+    p->filter = (w >= 0 && ord == GC_ORDER_GRAY);
+    p->N = (w < 0 || ord == GC_ORDER_GRAY) ? (1ull << n) : binom64(n, w);
+    p->valid = (w < 0) ? (1ull << n) : binom64(n, w);
+    // sphere packing: radius floor((d-1)/2) balls around codewords are disjoint
+    const int t = d >= 1 ? (d - 1) / 2 : 0;
+    const uint64_t hb = (1ull << n) / ball_volume(n, t);
+    p->bound = std::max<uint64_t>(1, std::min<uint64_t>(p->valid, hb));
+    if (d <= 1) p->bound = p->valid;
+    return true;
+}
+
+// Strategy choice.  Distance strategy cost ~ executed popcount tests;
+// bitmap strategy cost ~ words OR-ed by ball marking (each an L2 atomic,
+// weighted as several tests) plus one lookup per candidate.  |C| is taken as
+// half the sphere-packing bound (lexicodes sit close to it).
+static void plan_for(const HostProblem& p, gc_plan_t* pl) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    pl->grid = sms > 0 ? sms : 1;
+    pl->block = 1024;
+    pl->window_min = 256;
+    pl->window_max = 0;
+    pl->survivor_target = 256;
+    if (p.d <= 1) {
+        pl->strategy = GC_STRATEGY_DISTANCE;
+        return;
+    }
+    const double N = (double)p.valid;
+    const double C = std::max(1.0, 0.5 * (double)p.bound);
+    const double space = std::ldexp(1.0, p.n);
+    const double V = (double)ball_volume(p.n, p.d - 1);
+    const double to_first_hit = std::max(1.0, std::min(C / 2.0, space / V));
+    const double dist_cost = N * to_first_hit + 2.0 * C * C / 2.0;
+    const double marks = C * (double)high_ball_len(p.n, p.d) / 2.0;
+    const double bitmap_cost = 8.0 * marks + N;
+    const double bitmap_bytes = space / 8.0;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const bool bitmap_ok = bitmap_bytes < 0.5 * (double)free_b && high_ball_len(p.n, p.d) < (1u << 24);
+    const bool dist_ok = p.bound < 0xffffffffull;
+    if (!dist_ok || (bitmap_ok && bitmap_cost < dist_cost))
+        pl->strategy = GC_STRATEGY_BITMAP;
+    else
+        pl->strategy = GC_STRATEGY_DISTANCE;
+    if (const char* e = std::getenv("GC_STRATEGY")) {
+        if (!std::strcmp(e, "distance")) pl->strategy = GC_STRATEGY_DISTANCE;
+        if (!std::strcmp(e, "bitmap")) pl->strategy = GC_STRATEGY_BITMAP;
+    }
+}
+
+static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* out) {
+    plan_for(p, out);
+    if (in) {
+        if (in->strategy != GC_STRATEGY_AUTO) out->strategy = in->strategy;
+        if (in->grid > 0) out->grid = in->grid;
+        if (in->window_min) out->window_min = in->window_min;
+        if (in->window_max) out->window_max = in->window_max;
+        if (in->survivor_target) out->survivor_target = in->survivor_target;
+    }
+    return out->strategy == GC_STRATEGY_DISTANCE || out->strategy == GC_STRATEGY_BITMAP;
+}
+
+static bool is_device_ptr(const void* ptr) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// d <= 1 with no weight filter: every candidate is accepted, in order.
+__global__ void all_accepted_stats(gc_stats* st, uint64_t N, int strategy) {
+    st->codewords = N;
+    st->candidates = N;
+    st->dense_tests = N * (N - 1) / 2;  // candidate i meets the i before it
+    st->executed_tests = 0;
+    st->marks = 0;
+    st->windows = 0;
+    st->survivors = 0;
+    st->status = 0;
+    st->strategy = strategy;
+}
+
+static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint32_t* d_out,
+                               uint64_t capacity, gc_stats* d_stats, void* ws, size_t ws_bytes,
+                               cudaStream_t s) {
+    if (p.d <= 1 && !p.filter) {
+        int rc = launch_unrank(p, 0, std::min(capacity, p.N), d_out, s);
+        if (rc) return rc;
+        all_accepted_stats<<<1, 1, 0, s>>>(d_stats, p.N, plan.strategy);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? GC_OK : fail(GC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    SweepLayout L;
+    std::string why;
+    if (!sweep_layout(p, plan, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
+    if (ws_bytes < L.total) return fail(GC_ERR_INVALID, "workspace too small");
+    if (((uintptr_t)ws & 255u) != 0) return fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
+    int rc = launch_sweep(p, plan, L, d_out, capacity, d_stats, ws, s, &why);
+    if (rc) return fail(rc, why);
+    return GC_OK;
+}
+
+}  // namespace gc
+
+using namespace gc;
+
+extern "C" {
+
+const char* gc_strerror(int err) {
+    switch (err) {
+        case GC_OK: return "ok";
+        case GC_ERR_INVALID: return "invalid argument";
+        case GC_ERR_CAPACITY: return "output capacity too small";
+        case GC_ERR_CUDA: return "CUDA error";
+        case GC_ERR_OOM: return "out of memory";
+        case GC_ERR_TIMEOUT: return "device-side wait timed out";
+        case GC_ERR_UNSUPPORTED: return "unsupported";
+        case GC_ERR_INTERNAL: return "internal error";
+        default: return "unknown error";
+    }
+}
+
+const char* gc_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t gc_candidate_count(int n, int w, int ordering) {
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, 2, ordering, w, &p, &why)) return 0;
+    return p.N;
+}
+
+uint64_t gc_capacity_bound(int n, int d, int w) {
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, d, GC_ORDER_LEX, w, &p, &why)) return 0;
+    return p.bound;
+}
+
+int gc_plan(const gc_problem* prob, gc_plan_t* out) {
+    if (!prob || !out) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why))
+        return fail(GC_ERR_INVALID, why);
+    plan_for(p, out);
+    return GC_OK;
+}
+
+size_t gc_workspace_size(const gc_problem* prob, const gc_plan_t* plan) {
+    if (!prob) return 0;
+    HostProblem p;
+    std::string why;
+    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why)) return 0;
+    gc_plan_t pl;
+    if (!resolve_plan(p, plan, &pl)) return 0;
+    if (p.d <= 1 && !p.filter) return 256;
+    SweepLayout L;
+    if (!sweep_layout(p, pl, &L, &why)) return 0;
+    return L.total;
+}
+
+int gc_generate_async(const gc_problem* prob, const gc_plan_t* plan, uint32_t* d_out,
+                      uint64_t capacity, gc_stats* d_stats, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    if (!prob || !d_stats || (!d_out && capacity > 0)) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why))
+        return fail(GC_ERR_INVALID, why);
+    gc_plan_t pl;
+    if (!resolve_plan(p, plan, &pl)) return fail(GC_ERR_INVALID, "bad strategy");
+    return generate_async_impl(p, pl, d_out, capacity, d_stats, workspace, workspace_bytes,
+                               (cudaStream_t)stream);
+}
+
+int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inout_count) {
+    if (!inout_count || (!out && *inout_count > 0)) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, d, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
+    gc_plan_t pl;
+    resolve_plan(p, nullptr, &pl);
+    const uint64_t cap = *inout_count;
+    const bool dev_out = cap > 0 && is_device_ptr(out);
+    size_t ws_bytes = 256;
+    if (!(p.d <= 1 && !p.filter)) {
+        SweepLayout L;
+        if (!sweep_layout(p, pl, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
+        ws_bytes = L.total;
+    }
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(GC_ERR_CUDA, "stream create");
+    void* ws = nullptr;
+    gc_stats* d_stats = nullptr;
+    uint32_t* d_buf = nullptr;
+    const uint64_t dcap = dev_out ? 0 : std::min<uint64_t>(cap, p.bound);
+    int rc = GC_OK;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&ws, ws_bytes, s)) != cudaSuccess ||
+        (e = cudaMallocAsync((void**)&d_stats, sizeof(gc_stats), s)) != cudaSuccess ||
+        (dcap && (e = cudaMallocAsync((void**)&d_buf, dcap * 4, s)) != cudaSuccess)) {
+        rc = fail(e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (!rc) rc = generate_async_impl(p, pl, dev_out ? out : d_buf, dev_out ? cap : dcap, d_stats,
+                                      ws, ws_bytes, s);
+    gc_stats st{};
+    if (!rc) {
+        if ((e = cudaMemcpyAsync(&st, d_stats, sizeof st, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            rc = fail(GC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (!rc && st.status != 0) rc = fail(st.status, "device-side error in the sweep");
+    if (!rc && !dev_out && dcap) {
+        const uint64_t ncopy = std::min<uint64_t>(st.codewords, dcap);
+        if ((e = cudaMemcpy(out, d_buf, ncopy * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            rc = fail(GC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (d_buf) cudaFreeAsync(d_buf, s);
+    if (d_stats) cudaFreeAsync(d_stats, s);
+    if (ws) cudaFreeAsync(ws, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    *inout_count = st.codewords;
+    if (st.codewords > cap) return fail(GC_ERR_CAPACITY, "output capacity too small");
+    return GC_OK;
+}
+
+int gc_unrank(int n, int ordering, int w, uint64_t rank0, uint64_t count, uint32_t* d_vec,
+              void* stream) {
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, 2, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
+    if (count > 0 && !d_vec) return fail(GC_ERR_INVALID, "null output");
+    if (rank0 > p.N || count > p.N - rank0) return fail(GC_ERR_INVALID, "rank out of range");
+    return launch_unrank(p, rank0, count, d_vec, (cudaStream_t)stream);
+}
+
+int gc_rank(int n, int ordering, const uint32_t* d_vec, uint64_t count, uint64_t* d_rank,
+            void* stream) {
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, 2, ordering, -1, &p, &why)) return fail(GC_ERR_INVALID, why);
+    if (count > 0 && (!d_vec || !d_rank)) return fail(GC_ERR_INVALID, "null pointer");
+    return launch_rank(n, ordering, d_vec, count, d_rank, (cudaStream_t)stream);
+}
+
+int gc_block_test(int d, const uint32_t* d_cand, uint64_t ncand, const uint32_t* d_code,
+                  uint64_t ncode, uint8_t* d_alive, void* stream) {
+    if (d < 0) return fail(GC_ERR_INVALID, "d must be >= 0");
+    if ((ncand && (!d_cand || !d_alive)) || (ncode && !d_code))
+        return fail(GC_ERR_INVALID, "null pointer");
+    return launch_block_test(d, d_cand, ncand, d_code, ncode, d_alive, (cudaStream_t)stream);
+}
+
+int gc_resolve(int d, const uint32_t* d_cand, uint32_t ncand, uint32_t* d_accepted,
+               uint32_t* d_count, void* stream) {
+    if (d < 0) return fail(GC_ERR_INVALID, "d must be >= 0");
+    if (!d_count || (ncand && (!d_cand || !d_accepted))) return fail(GC_ERR_INVALID, "null pointer");
+    return launch_resolve(d, d_cand, ncand, d_accepted, d_count, (cudaStream_t)stream);
+}
+
+int gc_bitmap_mark(int n, int d, const uint32_t* d_code, uint64_t ncode, uint32_t* d_bitmap,
+                   void* stream) {
+    if (n < 1 || n > 32 || d < 0) return fail(GC_ERR_INVALID, "bad n or d");
+    if (ncode && (!d_code || !d_bitmap)) return fail(GC_ERR_INVALID, "null pointer");
+    if (ncode == 0 || d == 0) return GC_OK;
+    const uint64_t hlen = high_ball_len(n, d);
+    if (hlen >= (1ull << 31)) return fail(GC_ERR_UNSUPPORTED, "ball too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&tmp, hlen * 4, s);
+    if (e != cudaSuccess) return fail(GC_ERR_OOM, cudaGetErrorString(e));
+    int rc = launch_bitmap_mark(n, d, d_code, ncode, d_bitmap, tmp, s);
+    cudaFreeAsync(tmp, s);
+    return rc;
+}
+
+int gc_bitmap_scan(int n, int ordering, int w, const uint32_t* d_bitmap, uint64_t rank0,
+                   uint64_t count, uint32_t* d_out, uint64_t capacity, uint64_t* d_found,
+                   void* stream) {
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, 2, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
+    if (!d_found || (count && !d_bitmap) || (capacity && !d_out))
+        return fail(GC_ERR_INVALID, "null pointer");
+    if (rank0 > p.N || count > p.N - rank0) return fail(GC_ERR_INVALID, "rank out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* counts = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&counts, sizeof(uint64_t) * kScanMaxBlocks, s);
+    if (e != cudaSuccess) return fail(GC_ERR_OOM, cudaGetErrorString(e));
+    int rc = launch_bitmap_scan(p, d_bitmap, rank0, count, d_out, capacity, d_found, counts, s);
+    cudaFreeAsync(counts, s);
+    return rc;
+}
+
+}  // extern "C"

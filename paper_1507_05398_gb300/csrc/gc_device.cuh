@@ -1,0 +1,169 @@
+// gc_device.cuh -- device-side building blocks of the greedy sweep (sm_103a).
+//
+// Vectors are the low n bits of a uint32 with coordinate 1 as the most
+// significant of them.  The four orders of Section 4.2 are turned into
+// closed-form rank <-> vector maps so that any window of ranks can be
+// generated in parallel without materialising the order:
+//   LEX      rank r is the vector r.
+//   GRAY     rank r is r ^ (r >> 1); the inverse is a prefix XOR.
+//   GRLEX    weight classes in ascending weight; inside class k the i-th
+//            vector is the i-th smallest n-bit integer of weight k, found with
+//            the combinatorial number system.
+//   GREVLEX  weight classes ascending; inside class k vectors are ordered by
+//            DECREASING bit-reversed value (the lowest differing bit decides
+//            and the vector holding the 1 comes first), so the i-th one is
+//            the bit-reversal of the (C(n,k)-1-i)-th smallest weight-k integer.
+#pragma once
+#include <cstdint>
+
+namespace gc {
+
+constexpr int kMaxN = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- binomials
+// Binomial coefficients C(p, k), 0 <= p, k <= 32, fit in uint32 (the largest,
+// C(32,16), is about 6.0e8).  Kept in shared memory by the kernels that use
+// them because the indices diverge across a warp.
+struct Binom {
+    uint32_t c[kMaxN + 1][kMaxN + 1];
+};
+
+__host__ __device__ inline void fill_binom(Binom& b) {
+    for (int p = 0; p <= kMaxN; ++p)
+        for (int k = 0; k <= kMaxN; ++k)
+            b.c[p][k] = (k == 0) ? 1u : (p == 0 ? 0u : b.c[p - 1][k - 1] + b.c[p - 1][k]);
+}
+
+// i-th (0-based) n-bit integer of weight k in ascending order.  Walking bit
+// positions from the top: the C(p, k) weight-k integers below 2^p come before
+// every one with bit p set, so bit p is set iff i >= C(p, k).
+__device__ __forceinline__ uint32_t comb_unrank(const uint32_t (*C)[kMaxN + 1], int n, int k,
+                                                uint32_t i) {
+    uint32_t x = 0;
+    for (int p = n - 1; p >= 0 && k > 0; --p) {
+        uint32_t c = C[p][k];
+        if (i >= c) {
+            x |= 1u << p;
+            i -= c;
+            --k;
+        }
+    }
+    return x;
+}
+
+// Position of x among the n-bit integers of its weight, ascending: with set
+// bits at p_1 < p_2 < ... < p_k the position is sum_j C(p_j, j).
+__device__ __forceinline__ uint32_t comb_rank(const uint32_t (*C)[kMaxN + 1], uint32_t x) {
+    uint32_t r = 0;
+    int j = 1;
+    while (x) {
+        int p = __ffs(x) - 1;
+        r += C[p][j];
+        ++j;
+        x &= x - 1;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t reverse_n(uint32_t v, int n) { return __brev(v) >> (32 - n); }
+
+__device__ __forceinline__ uint32_t gray_inverse(uint32_t g) {
+    g ^= g >> 1;
+    g ^= g >> 2;
+    g ^= g >> 4;
+    g ^= g >> 8;
+    g ^= g >> 16;
+    return g;
+}
+
+// ---------------------------------------------------------------- orders
+enum : int { kLex = 0, kGray = 1, kGrlex = 2, kGrevlex = 3 };
+
+// Everything the ordering maps need, small enough to pass by value.
+struct Order {
+    int n;
+    int ord;
+    int w;          // -1 = every weight
+    bool filter;    // ranks whose vector has the wrong weight are skipped
+    uint64_t N;     // rank-space size
+    // graded orders without a weight: cum[k] = number of vectors of weight < k
+    uint64_t cum[kMaxN + 2];
+};
+
+// Vector of rank r (r < N).  Returns false for a Gray rank of the wrong weight.
+__device__ __forceinline__ bool unrank(const Order& o, const uint32_t (*C)[kMaxN + 1], uint64_t r,
+                                       uint32_t& x) {
+    const int n = o.n;
+    if (o.ord == kGray) {
+        x = (uint32_t)(r ^ (r >> 1));
+        return !o.filter || __popc(x) == o.w;
+    }
+    if (o.ord == kLex && o.w < 0) {
+        x = (uint32_t)r;
+        return true;
+    }
+    int k;
+    uint32_t i;
+    if (o.w >= 0) {
+        k = o.w;
+        i = (uint32_t)r;
+    } else {
+        // weight class of r: the last k with cum[k] <= r (classes ascend)
+        k = 0;
+        while (k < n && o.cum[k + 1] <= r) ++k;
+        i = (uint32_t)(r - o.cum[k]);
+    }
+    if (o.ord == kGrevlex) {
+        uint32_t m = C[n][k] - 1 - i;
+        x = reverse_n(comb_unrank(C, n, k, m), n);
+    } else {
+        x = comb_unrank(C, n, k, i);  // kGrlex, or kLex restricted to weight w
+    }
+    return true;
+}
+
+// Rank of vector x in the full 2^n order (no weight).
+__device__ __forceinline__ uint64_t rank_of(const Order& o, const uint32_t (*C)[kMaxN + 1],
+                                            uint32_t x) {
+    const int n = o.n;
+    switch (o.ord) {
+        case kLex: return x;
+        case kGray: return gray_inverse(x);
+        default: {
+            int k = __popc(x);
+            uint64_t base = 0;
+            for (int j = 0; j < k; ++j) base += C[n][j];
+            uint32_t pos = (o.ord == kGrlex) ? comb_rank(C, x)
+                                             : C[n][k] - 1 - comb_rank(C, reverse_n(x, n));
+            return base + pos;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- memory ops
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+// Loads of data other CTAs wrote during this kernel: L2 only (L1 is not
+// coherent across SMs).
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------- warp utils
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+}  // namespace gc

@@ -1,0 +1,69 @@
+// gc_internal.h -- host-side interfaces between the C ABI (gc_capi.cu) and
+// the kernel launchers (gc_sweep.cu, gc_steps.cu).  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/gc.h"
+
+namespace gc {
+
+// Fully checked problem description shared by the launchers.
+struct HostProblem {
+    int n, d, ord, w;
+    bool filter;       // GRAY with a weight: ranks of the wrong weight skipped
+    uint64_t N;        // rank-space size
+    uint64_t valid;    // number of candidates (C(n,w) or 2^n)
+    uint64_t bound;    // gc_capacity_bound
+};
+
+uint64_t binom64(int n, int k);
+bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why);
+
+// Word-grouped ball: entries (e_high << 3) | radius for every high part of
+// weight <= d-1 over the n-5 word-index bits; radius = d-1-weight(e_high),
+// clipped to 7.  Its length:
+uint64_t high_ball_len(int n, int d);
+int launch_high_ball(int nh, int rad, uint32_t* d_out, uint32_t len, cudaStream_t s);
+
+struct SweepLayout {
+    int grid;
+    uint32_t cache_words;   // shared-memory code cache (distance strategy)
+    size_t smem_bytes;
+    uint64_t store_words;   // global code store (distance strategy)
+    size_t off_bar, off_segcnt, off_segx, off_segoff, off_store, off_bitmap, off_hball;
+    size_t total;
+};
+
+// Fills the workspace layout for a problem and plan; returns false with a
+// reason if the plan cannot run (e.g. the bitmap would not fit).
+bool sweep_layout(const HostProblem& p, const gc_plan_t& plan, SweepLayout* L, std::string* why);
+
+// Launches the sweep (and its set-up kernels) on stream; returns a GC_* code.
+int launch_sweep(const HostProblem& p, const gc_plan_t& plan, const SweepLayout& L,
+                 uint32_t* d_out, uint64_t capacity, gc_stats* d_stats, void* workspace,
+                 cudaStream_t stream, std::string* why);
+
+// Step launchers (gc_steps.cu); each returns a GC_* code.
+int launch_unrank(const HostProblem& p, uint64_t rank0, uint64_t count, uint32_t* d_vec,
+                  cudaStream_t s);
+int launch_rank(int n, int ord, const uint32_t* d_vec, uint64_t count, uint64_t* d_rank,
+                cudaStream_t s);
+int launch_block_test(int d, const uint32_t* d_cand, uint64_t ncand, const uint32_t* d_code,
+                      uint64_t ncode, uint8_t* d_alive, cudaStream_t s);
+int launch_resolve(int d, const uint32_t* d_cand, uint32_t ncand, uint32_t* d_acc,
+                   uint32_t* d_count, cudaStream_t s);
+int launch_bitmap_mark(int n, int d, const uint32_t* d_code, uint64_t ncode, uint32_t* d_bitmap,
+                       uint32_t* d_hball_scratch, cudaStream_t s);
+constexpr int kScanMaxBlocks = 1024;  // d_counts must hold this many uint64
+int launch_bitmap_scan(const HostProblem& p, const uint32_t* d_bitmap, uint64_t rank0,
+                       uint64_t count, uint32_t* d_out, uint64_t capacity, uint64_t* d_found,
+                       uint64_t* d_counts, cudaStream_t s);
+
+// Records a message for gc_last_error() and returns code.
+int fail(int code, const std::string& msg);
+
+}  // namespace gc

@@ -1,0 +1,313 @@
+"""ctypes binding of libgc (include/gc.h): argument marshalling only.
+
+Every step of the sweep runs in the CUDA kernels of libgc.so; nothing here
+computes codes.  Device buffers are torch CUDA tensors; the stream is torch's
+current stream unless one is given.  If the library is missing the import of
+any entry point raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+__all__ = [
+    "LEX", "GRAY", "GRLEX", "GREVLEX", "NO_WEIGHT", "ORDERS",
+    "STRATEGY_AUTO", "STRATEGY_DISTANCE", "STRATEGY_BITMAP",
+    "GcError", "Problem", "Plan", "Stats", "lib", "library_path", "header_functions",
+    "strerror", "candidate_count", "capacity_bound", "plan", "workspace_size",
+    "generate", "generate_async", "generate_host",
+    "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
+    "probe_test_rate", "stats_from",
+]
+
+LEX, GRAY, GRLEX, GREVLEX = 0, 1, 2, 3
+NO_WEIGHT = -1
+ORDERS = {"lex": LEX, "gray": GRAY, "grlex": GRLEX, "grevlex": GREVLEX}
+STRATEGY_AUTO, STRATEGY_DISTANCE, STRATEGY_BITMAP = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "gc.h")
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libgc.so")
+
+
+class GcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code}): {_last_error()}")
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("d", ctypes.c_int), ("ordering", ctypes.c_int),
+                ("weight", ctypes.c_int)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int), ("grid", ctypes.c_int), ("block", ctypes.c_int),
+                ("window_min", ctypes.c_uint32), ("window_max", ctypes.c_uint32),
+                ("survivor_target", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("codewords", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("dense_tests", ctypes.c_uint64), ("executed_tests", ctypes.c_uint64),
+                ("marks", ctypes.c_uint64), ("windows", ctypes.c_uint64),
+                ("survivors", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("strategy", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_u64, _i32, _u32, _vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p
+_SIGS = {
+    "gc_strerror": (ctypes.c_char_p, [_i32]),
+    "gc_last_error": (ctypes.c_char_p, []),
+    "gc_candidate_count": (_u64, [_i32, _i32, _i32]),
+    "gc_capacity_bound": (_u64, [_i32, _i32, _i32]),
+    "gc_plan": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan)]),
+    "gc_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Problem), ctypes.POINTER(Plan)]),
+    "gc_generate": (_i32, [_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_u64)]),
+    "gc_generate_async": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan), _vp, _u64, _vp,
+                                 _vp, ctypes.c_size_t, _vp]),
+    "gc_unrank": (_i32, [_i32, _i32, _i32, _u64, _u64, _vp, _vp]),
+    "gc_rank": (_i32, [_i32, _i32, _vp, _u64, _vp, _vp]),
+    "gc_block_test": (_i32, [_i32, _vp, _u64, _vp, _u64, _vp, _vp]),
+    "gc_resolve": (_i32, [_i32, _vp, _u32, _vp, _vp, _vp]),
+    "gc_bitmap_mark": (_i32, [_i32, _i32, _vp, _u64, _vp, _vp]),
+    "gc_bitmap_scan": (_i32, [_i32, _i32, _i32, _vp, _u64, _u64, _vp, _u64, _vp, _vp]),
+    "gc_probe_test_rate": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/gc.h declares."""
+    text = open(_HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gc_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib():
+    """Load libgc.so (build it first if a toolchain is present)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                from . import build as _build
+                _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().gc_strerror(code).decode()
+
+
+def _last_error() -> str:
+    return lib().gc_last_error().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise GcError(rc, what)
+
+
+def _ord(o) -> int:
+    return ORDERS[o] if isinstance(o, str) else int(o)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_u32(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype in (torch.int32, torch.uint32)):
+        raise TypeError("expected a CUDA tensor of 32-bit words")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t
+
+
+# ---------------------------------------------------------------- information
+def candidate_count(n: int, weight: int = NO_WEIGHT, ordering="lex") -> int:
+    return int(lib().gc_candidate_count(n, weight, _ord(ordering)))
+
+
+def capacity_bound(n: int, d: int, weight: int = NO_WEIGHT) -> int:
+    return int(lib().gc_capacity_bound(n, d, weight))
+
+
+def _problem(n, d, ordering, weight):
+    return Problem(n, d, _ord(ordering), weight)
+
+
+def plan(n: int, d: int, ordering="lex", weight: int = NO_WEIGHT) -> Plan:
+    p = Plan()
+    _check(lib().gc_plan(ctypes.byref(_problem(n, d, ordering, weight)), ctypes.byref(p)),
+           "gc_plan")
+    return p
+
+
+def _plan_arg(strategy=None, **kw):
+    if strategy is None and not kw:
+        return None
+    p = Plan()
+    p.strategy = {None: 0, "auto": 0, "distance": 1, "bitmap": 2}.get(strategy, strategy or 0)
+    for k, v in kw.items():
+        if v is not None:
+            setattr(p, k, v)
+    return p
+
+
+def workspace_size(n, d, ordering="lex", weight=NO_WEIGHT, strategy=None, **plan_kw) -> int:
+    pl = _plan_arg(strategy, **plan_kw)
+    return int(lib().gc_workspace_size(ctypes.byref(_problem(n, d, ordering, weight)),
+                                       ctypes.byref(pl) if pl is not None else None))
+
+
+# ---------------------------------------------------------------- the sweep
+def generate_async(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, workspace,
+                   strategy=None, stream=None, **plan_kw):
+    """gc_generate_async: out (uint32 CUDA tensor, its length is the capacity),
+    stats (uint8 CUDA tensor of sizeof(gc_stats) bytes), workspace (uint8 CUDA
+    tensor of >= workspace_size bytes, 256-byte aligned)."""
+    pl = _plan_arg(strategy, **plan_kw)
+    rc = lib().gc_generate_async(ctypes.byref(_problem(n, d, ordering, weight)),
+                                 ctypes.byref(pl) if pl is not None else None,
+                                 _ptr(out), out.numel() if out is not None else 0, _ptr(stats),
+                                 _ptr(workspace), workspace.numel(), _stream(stream))
+    _check(rc, "gc_generate_async")
+
+
+def stats_from(t) -> Stats:
+    """Decode a stats tensor (device or host) into a Stats struct."""
+    raw = bytes(t.cpu().numpy().tobytes())
+    return Stats.from_buffer_copy(raw[:ctypes.sizeof(Stats)])
+
+
+def generate(n, d, ordering="lex", weight=NO_WEIGHT, *, strategy=None, stream=None,
+             capacity=None, return_stats=False, **plan_kw):
+    """Whole sweep on the current CUDA device; returns a uint32 CUDA tensor
+    with the code in acceptance order (and the Stats if asked)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cap = capacity_bound(n, d, weight) if capacity is None else capacity
+    ws_bytes = workspace_size(n, d, ordering, weight, strategy, **plan_kw)
+    if ws_bytes == 0:
+        raise GcError(1, "gc_workspace_size")
+    out = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    st = torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    base = (-ws.data_ptr()) % 256
+    ws_al = ws[base:base + ws_bytes]
+    generate_async(n, d, ordering, weight, out=out[:cap] if cap else None, stats=st,
+                   workspace=ws_al, strategy=strategy, stream=stream, **plan_kw)
+    s = stats_from(st)
+    if s.status != 0:
+        raise GcError(int(s.status), "sweep")
+    code = out[:min(s.codewords, cap)]
+    return (code, s) if return_stats else code
+
+
+def generate_host(n, d, ordering="lex", weight=NO_WEIGHT, capacity=None) -> np.ndarray:
+    """gc_generate with a host buffer (the library allocates and copies)."""
+    cap = capacity_bound(n, d, weight) if capacity is None else capacity
+    buf = np.empty(max(cap, 1), dtype=np.uint32)
+    cnt = _u64(cap)
+    rc = lib().gc_generate(n, d, _ord(ordering), weight,
+                           buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt))
+    _check(rc, "gc_generate")
+    return buf[:cnt.value].copy()
+
+
+# ---------------------------------------------------------------- the steps
+def unrank(n, ordering, weight, rank0, count, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(max(count, 1), dtype=torch.int32, device="cuda")
+    _check(lib().gc_unrank(n, _ord(ordering), weight, rank0, count, _ptr(_dev_u32(out)),
+                           _stream(stream)), "gc_unrank")
+    return out[:count]
+
+
+def rank(n, ordering, vectors, stream=None):
+    import torch
+    v = _dev_u32(vectors)
+    out = torch.empty(max(v.numel(), 1), dtype=torch.int64, device=v.device)
+    _check(lib().gc_rank(n, _ord(ordering), _ptr(v), v.numel(), _ptr(out), _stream(stream)),
+           "gc_rank")
+    return out[:v.numel()]
+
+
+def block_test(d, cand, code, stream=None):
+    import torch
+    c = _dev_u32(cand)
+    k = _dev_u32(code)
+    alive = torch.empty(max(c.numel(), 1), dtype=torch.uint8, device=c.device)
+    _check(lib().gc_block_test(d, _ptr(c), c.numel(), _ptr(k), k.numel(), _ptr(alive),
+                               _stream(stream)), "gc_block_test")
+    return alive[:c.numel()]
+
+
+def resolve(d, cand, stream=None):
+    import torch
+    c = _dev_u32(cand)
+    acc = torch.empty(max(c.numel(), 1), dtype=torch.int32, device=c.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=c.device)
+    _check(lib().gc_resolve(d, _ptr(c), c.numel(), _ptr(acc), _ptr(cnt), _stream(stream)),
+           "gc_resolve")
+    return acc[:int(cnt.item())]
+
+
+def bitmap_mark(n, d, code, bitmap=None, stream=None):
+    import torch
+    k = _dev_u32(code)
+    if bitmap is None:
+        bitmap = torch.zeros(max(((1 << n) + 31) // 32, 1), dtype=torch.int32, device=k.device)
+    _check(lib().gc_bitmap_mark(n, d, _ptr(k), k.numel(), _ptr(_dev_u32(bitmap)),
+                                _stream(stream)), "gc_bitmap_mark")
+    return bitmap
+
+
+def bitmap_scan(n, ordering, weight, bitmap, rank0, count, capacity=None, stream=None):
+    import torch
+    b = _dev_u32(bitmap)
+    cap = count if capacity is None else capacity
+    out = torch.empty(max(cap, 1), dtype=torch.int32, device=b.device)
+    found = torch.zeros(1, dtype=torch.int64, device=b.device)
+    _check(lib().gc_bitmap_scan(n, _ord(ordering), weight, _ptr(b), rank0, count, _ptr(out), cap,
+                                _ptr(found), _stream(stream)), "gc_bitmap_scan")
+    f = int(found.item())
+    return out[:min(f, cap)], f
+
+
+def probe_test_rate() -> tuple[float, float]:
+    """(distance tests per second with register operands, reported SM clock Hz)."""
+    r, c = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().gc_probe_test_rate(ctypes.byref(r), ctypes.byref(c)), "gc_probe_test_rate")
+    return r.value, c.value

@@ -1,0 +1,135 @@
+"""Parity of the whole CUDA sweep with the CPU oracle, element by element and
+in acceptance order, through the C ABI (gc_generate_async / gc_generate)."""
+import hashlib
+import json
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+ORDERS = ["lex", "gray", "grlex", "grevlex"]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def G():
+    import paper_1507_05398_gb300 as g
+    return g
+
+
+def gpu_code(n, d, o, w=-1, strategy=None, **kw):
+    code, st = G().generate(n, d, o, w, strategy=strategy, return_stats=True, **kw)
+    assert st.status == 0
+    return code.cpu().numpy().view(np.uint32), st
+
+
+@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_exhaustive_small(strategy, ordname):
+    """Every n <= 10, every d in [0, n+1], with and without a weight."""
+    for n in range(1, 11):
+        for d in range(0, n + 2):
+            for w in ([-1, n // 2, n] if n >= 2 else [-1, 0]):
+                want = oracle.greedy_pairwise(n, d, ordname, w)
+                got, st = gpu_code(n, d, ordname, w, strategy)
+                assert got.tolist() == want.tolist(), (n, d, ordname, w, strategy)
+                assert st.codewords == len(want)
+
+
+@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+def test_config_hamming_15(strategy):
+    """n = 15, d = 3, lex: the [15,11,3] Hamming code, 2048 words, XOR-closed."""
+    got, st = gpu_code(15, 3, "lex", -1, strategy)
+    assert got.tolist() == oracle.greedy_pairwise(15, 3, "lex").tolist()
+    assert len(got) == 2048
+    s = set(got.tolist())
+    assert all((int(a) ^ int(b)) in s for a in got[:64] for b in got)
+
+
+def test_config_golay_24():
+    """n = 24, d = 8, lex: extended Golay, 4096 words (the benchmark's first
+    code, in the benchmark's launch configuration)."""
+    got, st = gpu_code(24, 8, "lex")
+    want, pos = oracle.greedy_ball(24, 8, "lex", with_pos=True)
+    assert got.tolist() == want.tolist()
+    assert st.dense_tests == oracle.dense_tests(pos, 1 << 24)
+
+
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_config_n20_d4(ordname):
+    """n = 20, d = 4 in the four orders (the rest of the benchmark workload)."""
+    got, st = gpu_code(20, 4, ordname)
+    want, pos = oracle.greedy_ball(20, 4, ordname, with_pos=True)
+    assert got.tolist() == want.tolist()
+    assert len(got) == 16384
+    assert st.dense_tests == oracle.dense_tests(pos, 1 << 20)
+
+
+@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("ordname", ORDERS)
+@pytest.mark.parametrize("n,d", [(16, 3), (17, 5), (18, 4), (19, 6), (21, 3)])
+def test_mid_sizes(strategy, ordname, n, d):
+    """Many windows, ragged tiles, survivor truncation."""
+    want = oracle.greedy_ball(n, d, ordname)
+    got, _ = gpu_code(n, d, ordname, -1, strategy)
+    assert got.tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("ordname", ORDERS)
+@pytest.mark.parametrize("n,d,w", [(16, 4, 5), (18, 6, 6), (20, 4, 3), (14, 3, 7), (22, 6, 4)])
+def test_constant_weight(strategy, ordname, n, d, w):
+    want = oracle.greedy_pairwise(n, d, ordname, w)
+    got, _ = gpu_code(n, d, ordname, w, strategy)
+    assert got.tolist() == want.tolist()
+    assert all(bin(int(x)).count("1") == w for x in got)
+
+
+@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+def test_small_windows_and_degenerate(strategy):
+    """Tiny windows force thousands of window steps; d = 2 keeps half the
+    space (survivors beyond the resolver's capacity every window)."""
+    for n, d, o in [(16, 2, "lex"), (14, 2, "grevlex"), (18, 2, "gray")]:
+        want = oracle.greedy_ball(n, d, o)
+        got, _ = gpu_code(n, d, o, -1, strategy)
+        assert got.tolist() == want.tolist()
+    want = oracle.greedy_ball(18, 5, "grlex")
+    got, _ = gpu_code(18, 5, "grlex", -1, strategy, window_min=32, window_max=64,
+                      survivor_target=8)
+    assert got.tolist() == want.tolist()
+
+
+def test_capacity_and_host_entry():
+    g = G()
+    want = oracle.greedy_pairwise(15, 3, "gray")
+    assert g.generate_host(15, 3, "gray").tolist() == want.tolist()
+    with pytest.raises(g.GcError) as e:
+        g.generate_host(15, 3, "gray", capacity=100)
+    assert e.value.code == 2
+    code = g.generate(15, 3, "gray", capacity=100)
+    assert code.cpu().numpy().view(np.uint32).tolist() == want[:100].tolist()
+
+
+def _large():
+    p = os.path.join(GOLDEN, "large_expected.json")
+    if not os.path.exists(p):
+        return []
+    return json.load(open(p))["codes"]
+
+
+@pytest.mark.parametrize("row", _large(), ids=lambda r: f"n{r['n']}d{r['d']}{r['ordering']}")
+def test_large_configs_against_stored_oracle(row):
+    """n = 31, d = 3 and n = 32, d = 4 (all orders), n = 28, d = 5 lex:
+    compared with the oracle's stored list digest, plus closed forms."""
+    n, d, o, w = row["n"], row["d"], row["ordering"], row["weight"]
+    strategies = ["bitmap", "distance"] if n == 28 else [None]
+    for strategy in strategies:
+        got, st = gpu_code(n, d, o, w, strategy)
+        assert len(got) == row["size"]
+        assert got[:8].tolist() == row["head"] and int(got[-1]) == row["last"]
+        assert hashlib.sha256(got.astype("<u4").tobytes()).hexdigest() == row["sha256"]
+    if (n, d, o) == (31, 3, "lex"):
+        assert len(got) == 2 ** 26 and np.all(np.diff(got.astype(np.int64)) > 0)
