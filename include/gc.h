@@ -161,6 +161,31 @@ int gc_generate_async(const gc_problem *prob, const gc_plan_t *plan,
                       uint32_t *d_out, uint64_t capacity, gc_stats *d_stats,
                       void *workspace, size_t workspace_bytes, void *stream);
 
+/* Allocation-free form of gc_generate_async (the paper has no counterpart;
+ * this is a service for callers).  Some callers cannot call cudaMalloc when
+ * they need a code: code running while a CUDA stream is being captured,
+ * runtimes without a device allocator, or processes whose device memory is
+ * owned by another framework's pool.  This entry point allocates nothing: the
+ * caller passes only the output (d_out, capacity words) and d_stats, and the
+ * sweep's scratch lives in one static device array of
+ * gc_noalloc_scratch_bytes() bytes (32 MiB) inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *  - Problems whose scratch (gc_workspace_size) exceeds that size are rejected
+ *    with GC_ERR_UNSUPPORTED and a message naming both sizes.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array and it keeps the last call's contents
+ *    (the parts that must start at zero are cleared by each call): calls
+ *    whose work overlaps on the GPU, on any streams or threads, race.
+ *  - Results are identical to gc_generate_async for the same problem/plan. */
+int gc_generate_noalloc(const gc_problem *prob, const gc_plan_t *plan,
+                        uint32_t *d_out, uint64_t capacity, gc_stats *d_stats,
+                        void *stream);
+
+/* Size in bytes of gc_generate_noalloc's static scratch array. */
+size_t gc_noalloc_scratch_bytes(void);
+
 /* ---- the steps of the sweep, callable one at a time (for tests and for
  *      callers composing their own pipeline) ------------------------------ */
 

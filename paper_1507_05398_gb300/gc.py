@@ -21,7 +21,7 @@ __all__ = [
     "strerror", "candidate_count", "capacity_bound", "plan", "workspace_size",
     "generate", "generate_async", "generate_host",
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
-    "probe_test_rate", "stats_from",
+    "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
 ]
 
 LEX, GRAY, GRLEX, GREVLEX = 0, 1, 2, 3
@@ -86,6 +86,9 @@ _SIGS = {
     "gc_bitmap_mark": (_i32, [_i32, _i32, _vp, _u64, _vp, _vp]),
     "gc_bitmap_scan": (_i32, [_i32, _i32, _i32, _vp, _u64, _u64, _vp, _u64, _vp, _vp]),
     "gc_probe_test_rate": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "gc_generate_noalloc": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan), _vp, _u64, _vp,
+                                   _vp]),
+    "gc_noalloc_scratch_bytes": (ctypes.c_size_t, []),
 }
 
 
@@ -202,6 +205,23 @@ def generate_async(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, worksp
                                  _ptr(out), out.numel() if out is not None else 0, _ptr(stats),
                                  _ptr(workspace), workspace.numel(), _stream(stream))
     _check(rc, "gc_generate_async")
+
+
+def generate_noalloc(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, strategy=None,
+                     stream=None, **plan_kw):
+    """gc_generate_noalloc: like generate_async but the library allocates
+    nothing -- its scratch is a static device array (see include/gc.h).  For
+    callers that cannot allocate device memory when they need a code."""
+    pl = _plan_arg(strategy, **plan_kw)
+    rc = lib().gc_generate_noalloc(ctypes.byref(_problem(n, d, ordering, weight)),
+                                   ctypes.byref(pl) if pl is not None else None,
+                                   _ptr(out), out.numel() if out is not None else 0, _ptr(stats),
+                                   _stream(stream))
+    _check(rc, "gc_generate_noalloc")
+
+
+def noalloc_scratch_bytes() -> int:
+    return int(lib().gc_noalloc_scratch_bytes())
 
 
 def stats_from(t) -> Stats:
