@@ -159,6 +159,12 @@ def run_ours(args):
     import numpy as np
     import torch
 
+    global WORKLOAD, WORKLOAD_NAME
+    if args.only:
+        n, d, o = args.only.split(",")
+        WORKLOAD = [(int(n), int(d), o)]
+        WORKLOAD_NAME = f"n={n} d={d} {o} (single code)"
+
     import paper_1507_05398_gb300 as G
 
     rank, world, local = dist_env()
@@ -225,8 +231,10 @@ def run_ours(args):
     value = world * dense / (mean_step_ms * 1e-3)
 
     # end to end through the public host API (allocation, sweep, copy back)
-    e2e_times, d2h = [], 0
-    for s in range(args.steps):
+    e2e_times, d2h = [float("nan")], 0
+    for s in range(0 if args.no_e2e else args.steps):
+        if s == 0:
+            e2e_times = []
         torch.cuda.synchronize()
         t = time.perf_counter()
         words = 0
@@ -284,6 +292,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API leg")
+    ap.add_argument("--only", default=None,
+                    help="run one code instead of the workload, e.g. '24,8,lex' (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -17,13 +17,15 @@ __global__ void __launch_bounds__(256) probe_popc_kernel(uint32_t seed, int iter
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = (seed + 977u * k) * (threadIdx.x + 131u * blockIdx.x + 1u);
     uint32_t c = seed ^ (threadIdx.x * 2654435761u);
-    uint32_t hit = 0;
+    uint32_t hits = 0;
     for (int i = 0; i < iters; ++i) {
         c = c * 1664525u + 1013904223u;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) hit |= (uint32_t)(__popc(x[k] ^ c) < d) << k;
+        for (int k = 0; k < 8; ++k) hits += (uint32_t)(__popc(x[k] ^ c) < d);
     }
-    if (hit == 0xdeadbeefu) sink[0] = hit;  // keeps the loop alive
+    // the count depends on every test and the seed is a run-time value, so
+    // the compiler cannot drop the loop
+    if (hits == seed) sink[0] = hits;
 }
 
 }  // namespace gc
