@@ -174,102 +174,116 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    probs = [(n, d, o, -1) for n, d, o in WORKLOAD]
+    ngroups = len(probs) if args.groups is None else args.groups
 
-    # resident buffers: outputs, stats and workspaces for the five codes
-    jobs = []
-    for n, d, o in WORKLOAD:
-        pl = G.plan(n, d, o)
-        cap = G.capacity_bound(n, d)
-        ws_bytes = G.workspace_size(n, d, o)
-        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
-        base = (-ws.data_ptr()) % 256
-        jobs.append({"n": n, "d": d, "o": o, "strategy": pl.strategy,
-                     "out": torch.empty(cap, dtype=torch.int32, device=dev),
-                     "stats": torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=dev),
-                     "ws": ws[base:base + ws_bytes]})
+    # resident buffers: the whole workload as one batch (one launch per step)
+    batch = G.BatchBuffers(probs, ngroups=ngroups)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def one_step(events=None):
-        for k, j in enumerate(jobs):
-            if events is not None:
-                events[k][0].record(stream)
-            G.generate_async(j["n"], j["d"], j["o"], out=j["out"], stats=j["stats"],
-                             workspace=j["ws"], stream=stream)
-            if events is not None:
-                events[k][1].record(stream)
-
     for _ in range(args.warmup):
-        one_step()
+        batch.launch(stream)
     torch.cuda.synchronize()
-    stats = [G.stats_from(j["stats"]) for j in jobs]
-    for s in stats:
-        if s.status != 0:
-            raise RuntimeError(f"sweep failed: {s.as_dict()}")
-    dense = sum(s.dense_tests for s in stats)
-    executed = sum(s.executed_tests for s in stats)
-    launches_per_step = sum(2 if j["strategy"] == G.STRATEGY_BITMAP else 1 for j in jobs)
+    results = batch.results()
+    for (code, st), p in zip(results, probs):
+        if st.status != 0:
+            raise RuntimeError(f"sweep failed for {p}: {st.as_dict()}")
+    dense = sum(st.dense_tests for _, st in results)
+    executed = sum(st.executed_tests for _, st in results)
+    nbitmap = len({(n, d) for (n, d, o, w), (_, st) in zip(probs, results) if st.strategy == 2})
+    launches_per_step = 1 + nbitmap  # the sweep + one ball-table kernel per (n, d)
 
-    # timed region: K steps, L2 flushed before each, CUDA events per code
-    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-           for _ in jobs] for _ in range(args.steps)]
+    # timed region: K steps, L2 flushed before each, CUDA events per step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.fill_(s & 0xff)
-            one_step(ev[s])
+            ev[s][0].record(stream)
+            batch.launch(stream)
+            ev[s][1].record(stream)
         torch.cuda.synchronize()
-    per_code_ms = [[ev[s][k][0].elapsed_time(ev[s][k][1]) for s in range(args.steps)]
-                   for k in range(len(jobs))]
-    step_ms = [sum(per_code_ms[k][s] for k in range(len(jobs))) for s in range(args.steps)]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
     mean_step_ms = statistics.mean(step_ms)
     if world > 1:
         t = torch.tensor([mean_step_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         mean_step_ms = float(t.item())
     value = world * dense / (mean_step_ms * 1e-3)
+    stats_now = [st for _, st in batch.results()]
 
-    # end to end through the public host API (allocation, sweep, copy back)
-    e2e_times, d2h = [float("nan")], 0
+    # the same codes one launch each (gc_generate_async), for comparison
+    singles = []
+    for n, d, o, w in probs:
+        cap = G.capacity_bound(n, d, w)
+        ws_bytes = G.workspace_size(n, d, o, w)
+        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+        base = (-ws.data_ptr()) % 256
+        singles.append((n, d, o, w, torch.empty(cap, dtype=torch.int32, device=dev),
+                        torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=dev),
+                        ws[base:base + ws_bytes]))
+    per_code_ms = {}
+    for n, d, o, w, out, st, ws in singles:
+        G.generate_async(n, d, o, w, out=out, stats=st, workspace=ws, stream=stream)
+        times = []
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.generate_async(n, d, o, w, out=out, stats=st, workspace=ws, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        per_code_ms[f"n={n} d={d} {o}"] = statistics.mean(times)
+    single_ms = sum(per_code_ms.values())
+
+    # end to end through the public API: generate_batch allocates (torch's
+    # caching allocator), launches, waits and copies every code to the host
+    e2e_times, d2h = [], 0
     for s in range(0 if args.no_e2e else args.steps):
-        if s == 0:
-            e2e_times = []
         torch.cuda.synchronize()
         t = time.perf_counter()
-        words = 0
-        for j in jobs:
-            words += len(G.generate_host(j["n"], j["d"], j["o"]))
+        res = G.generate_batch(probs, ngroups=ngroups)
         e2e_times.append(time.perf_counter() - t)
-        d2h = words * 4 + ctypes.sizeof(G.Stats) * len(jobs)
-    e2e_value = world * dense / statistics.mean(e2e_times)
+        d2h = sum(len(c) * 4 for c, _ in res) + ctypes.sizeof(G.Stats) * len(res)
+    e2e_value = world * dense / statistics.mean(e2e_times) if e2e_times else None
 
-    # roofline of the sweep kernel: executed tests per second against the
-    # measured register-operand test rate of this GPU
+    # roofline of the sweep kernel: executed distance tests per second against
+    # the measured register-operand test rate of this GPU
     peak, _ = G.probe_test_rate()
-    sweep_s = mean_step_ms * 1e-3
-    achieved = executed / sweep_s
+    achieved = executed / (mean_step_ms * 1e-3)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     cpu = cpu_baseline_sample() if world == 1 and not args.no_cpu else None
+    clock_hz = 1e6 * (clk.summary()["sm_mhz"] or 2070.0)
     line = {
         "metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (fully determined by n, d, order)",
-        "config": {"workload": WORKLOAD_NAME, "codes_per_step": len(jobs),
+        "config": {"workload": WORKLOAD_NAME, "codes_per_step": len(probs),
+                   "launch": f"one batched persistent launch, {ngroups} SM groups",
                    "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "strategies": {f"n={j['n']} d={j['d']} {j['o']}":
-                                  ("bitmap" if j["strategy"] == 2 else "distance") for j in jobs}},
-        "per_code_ms": {f"n={j['n']} d={j['d']} {j['o']}": statistics.mean(per_code_ms[k])
-                        for k, j in enumerate(jobs)},
+                   "strategies": {f"n={n} d={d} {o}": ("bitmap" if st.strategy == 2 else "distance")
+                                  for (n, d, o, w), st in zip(probs, stats_now)}},
+        "one_launch_per_code_ms": per_code_ms,
+        "one_launch_per_code_ms_per_step": single_ms,
+        "batched_speedup_vs_one_launch_per_code": single_ms / mean_step_ms,
         "dense_tests_per_step": dense, "executed_tests_per_step": executed,
-        "executed_tests_per_s": executed / sweep_s,
+        "windows_per_step": sum(st.windows for st in stats_now),
+        "survivors_per_step": sum(st.survivors for st in stats_now),
+        "phase_ms_cta0": {f"n={n} d={d} {o}": dict(
+            {ph: round(1e3 * c / clock_hz, 4) for ph, c in zip(G.Stats.PHASES, st.phase_cycles)},
+            windows=st.windows, survivors=st.survivors)
+            for (n, d, o, w), st in zip(probs, stats_now)},
         "e2e": {"value": e2e_value, "unit": "tests/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(e2e_times)},
+                "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * statistics.mean(e2e_times) if e2e_times else None},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "tests/s",
                      "frac": achieved / peak, "traffic": None,
@@ -293,6 +307,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API leg")
+    ap.add_argument("--groups", type=int, default=None,
+                    help="SM groups of the batched launch (default: one per code)")
     ap.add_argument("--only", default=None,
                     help="run one code instead of the workload, e.g. '24,8,lex' (profiling)")
     args = ap.parse_args()

@@ -105,6 +105,12 @@ typedef struct {
     uint64_t survivors;        /* candidates that reached the resolver */
     int32_t status;            /* GC_OK or GC_ERR_TIMEOUT / _INTERNAL */
     int32_t strategy;          /* strategy that ran */
+    /* Diagnostic: SM cycles the first CTA of the job's group spent, summed
+     * over windows, in [0] ball marking, [1] candidate generation and bitmap
+     * lookup, [2] the newest-codeword test and compaction, [3] the split test
+     * against older codewords, [4] publishing and waiting for the group,
+     * [5] gathering survivors, [6] resolving, [7] committing. */
+    uint64_t phase_cycles[8];
 } gc_stats;
 
 /* ---- information ------------------------------------------------------ */
@@ -160,6 +166,33 @@ int gc_generate(int n, int d, int ordering, int weight_or_none,
 int gc_generate_async(const gc_problem *prob, const gc_plan_t *plan,
                       uint32_t *d_out, uint64_t capacity, gc_stats *d_stats,
                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- batches: many codes in one launch --------------------------------- */
+
+/* One code of a batch. */
+typedef struct {
+    gc_problem prob;
+    int strategy;          /* gc_strategy; AUTO = gc_plan()'s choice */
+    uint32_t *d_out;       /* device, capacity words, acceptance order */
+    uint64_t capacity;
+    gc_stats *d_stats;     /* device, one block per job */
+} gc_job;
+
+/* Device bytes of scratch gc_batch_generate_async() needs (0 if invalid).
+ * ngroups as for gc_batch_generate_async. */
+size_t gc_batch_workspace_size(const gc_job *jobs, int njobs, int ngroups);
+
+/* Generates every job's code (Section 3) in ONE persistent cooperative
+ * launch.  The SMs are split into ngroups groups of equal size (ngroups <= 0:
+ * one group per job, at most one per SM); jobs are assigned to groups longest
+ * first (by an estimate of their work) and each group sweeps its jobs one
+ * after the other, so independent codes run concurrently on disjoint SMs.
+ * Each job's result equals what gc_generate_async gives for it alone.
+ * workspace: device, >= gc_batch_workspace_size() bytes, 256-byte aligned,
+ * owned by the caller.  Per-job status is in its gc_stats. */
+int gc_batch_generate_async(const gc_job *jobs, int njobs, int ngroups,
+                            void *workspace, size_t workspace_bytes,
+                            void *stream);
 
 /* Allocation-free form of gc_generate_async (the paper has no counterpart;
  * this is a service for callers).  Some callers cannot call cudaMalloc when

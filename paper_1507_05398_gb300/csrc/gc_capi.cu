@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "gc_internal.h"
 
@@ -125,6 +126,7 @@ __global__ void all_accepted_stats(gc_stats* st, uint64_t N, int strategy) {
     st->survivors = 0;
     st->status = 0;
     st->strategy = strategy;
+    for (int k = 0; k < 8; ++k) st->phase_cycles[k] = 0;
 }
 
 static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint32_t* d_out,
@@ -137,13 +139,46 @@ static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? GC_OK : fail(GC_ERR_CUDA, cudaGetErrorString(e));
     }
-    SweepLayout L;
+    BatchJob job{p, plan, d_out, capacity, d_stats};
+    BatchLayout L;
     std::string why;
-    if (!sweep_layout(p, plan, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
+    if (!batch_layout(&job, 1, 1, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
     if (ws_bytes < L.total) return fail(GC_ERR_INVALID, "workspace too small");
     if (((uintptr_t)ws & 255u) != 0) return fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
-    int rc = launch_sweep(p, plan, L, d_out, capacity, d_stats, ws, s, &why);
+    int rc = launch_batch(&job, 1, L, ws, s, &why);
     if (rc) return fail(rc, why);
+    return GC_OK;
+}
+
+static size_t single_workspace(const HostProblem& p, const gc_plan_t& pl, std::string* why) {
+    if (p.d <= 1 && !p.filter) return 256;
+    BatchJob job{p, pl, nullptr, 0, nullptr};
+    BatchLayout L;
+    if (!batch_layout(&job, 1, 1, &L, why)) return 0;
+    return L.total;
+}
+
+// Checks and plans every job of a batch.
+static int make_batch(const gc_job* jobs, int njobs, std::vector<BatchJob>* out) {
+    if (!jobs || njobs < 1) return fail(GC_ERR_INVALID, "no jobs");
+    out->clear();
+    for (int j = 0; j < njobs; ++j) {
+        const gc_job& J = jobs[j];
+        BatchJob B{};
+        std::string why;
+        if (!make_problem(J.prob.n, J.prob.d, J.prob.ordering, J.prob.weight, &B.p, &why))
+            return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": " + why);
+        gc_plan_t in{};
+        in.strategy = J.strategy;
+        if (!resolve_plan(B.p, &in, &B.plan))
+            return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": bad strategy");
+        if (!J.d_stats || (!J.d_out && J.capacity > 0))
+            return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": null pointer");
+        B.d_out = J.d_out;
+        B.capacity = J.capacity;
+        B.d_stats = J.d_stats;
+        out->push_back(B);
+    }
     return GC_OK;
 }
 
@@ -200,10 +235,7 @@ size_t gc_workspace_size(const gc_problem* prob, const gc_plan_t* plan) {
     if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why)) return 0;
     gc_plan_t pl;
     if (!resolve_plan(p, plan, &pl)) return 0;
-    if (p.d <= 1 && !p.filter) return 256;
-    SweepLayout L;
-    if (!sweep_layout(p, pl, &L, &why)) return 0;
-    return L.total;
+    return single_workspace(p, pl, &why);
 }
 
 int gc_generate_async(const gc_problem* prob, const gc_plan_t* plan, uint32_t* d_out,
@@ -229,12 +261,8 @@ int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inou
     resolve_plan(p, nullptr, &pl);
     const uint64_t cap = *inout_count;
     const bool dev_out = cap > 0 && is_device_ptr(out);
-    size_t ws_bytes = 256;
-    if (!(p.d <= 1 && !p.filter)) {
-        SweepLayout L;
-        if (!sweep_layout(p, pl, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
-        ws_bytes = L.total;
-    }
+    const size_t ws_bytes = single_workspace(p, pl, &why);
+    if (ws_bytes == 0) return fail(GC_ERR_UNSUPPORTED, why);
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
         return fail(GC_ERR_CUDA, "stream create");
@@ -272,6 +300,30 @@ int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inou
     *inout_count = st.codewords;
     if (st.codewords > cap) return fail(GC_ERR_CAPACITY, "output capacity too small");
     return GC_OK;
+}
+
+size_t gc_batch_workspace_size(const gc_job* jobs, int njobs, int ngroups) {
+    std::vector<BatchJob> B;
+    if (make_batch(jobs, njobs, &B)) return 0;
+    BatchLayout L;
+    std::string why;
+    if (!batch_layout(B.data(), njobs, ngroups, &L, &why)) return 0;
+    return L.total;
+}
+
+int gc_batch_generate_async(const gc_job* jobs, int njobs, int ngroups, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    std::vector<BatchJob> B;
+    int rc = make_batch(jobs, njobs, &B);
+    if (rc) return rc;
+    BatchLayout L;
+    std::string why;
+    if (!batch_layout(B.data(), njobs, ngroups, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
+    if (!workspace || workspace_bytes < L.total) return fail(GC_ERR_INVALID, "workspace too small");
+    if (((uintptr_t)workspace & 255u) != 0)
+        return fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
+    rc = launch_batch(B.data(), njobs, L, workspace, (cudaStream_t)stream, &why);
+    return rc ? fail(rc, why) : GC_OK;
 }
 
 int gc_unrank(int n, int ordering, int w, uint64_t rank0, uint64_t count, uint32_t* d_vec,

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/gc.h"
 
@@ -29,22 +30,35 @@ bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* w
 uint64_t high_ball_len(int n, int d);
 int launch_high_ball(int nh, int rad, uint32_t* d_out, uint32_t len, cudaStream_t s);
 
-struct SweepLayout {
-    int grid;
-    uint32_t cache_words;   // shared-memory code cache (distance strategy)
-    size_t smem_bytes;
-    uint64_t store_words;   // global code store (distance strategy)
-    size_t off_bar, off_segcnt, off_segx, off_segoff, off_store, off_bitmap, off_hball;
-    size_t total;
+// One job of a batch, checked and planned on the host.
+struct BatchJob {
+    HostProblem p;
+    gc_plan_t plan;     // strategy is DISTANCE or BITMAP here
+    uint32_t* d_out;
+    uint64_t capacity;
+    gc_stats* d_stats;
 };
 
-// Fills the workspace layout for a problem and plan; returns false with a
-// reason if the plan cannot run (e.g. the bitmap would not fit).
-bool sweep_layout(const HostProblem& p, const gc_plan_t& plan, SweepLayout* L, std::string* why);
+// Where everything of a batched sweep lives: CTA groups, their jobs, and
+// the workspace offsets of the descriptors and scratch.
+struct BatchLayout {
+    int grid = 0, ngroups = 0;
+    uint32_t cache_words = 0;   // shared-memory code cache (distance jobs)
+    size_t smem_bytes = 0;
+    std::vector<int> first_cta, ncta, job_begin, job_end, job_order;
+    size_t off_err = 0, off_jobs = 0, off_order = 0, off_groups = 0;
+    std::vector<size_t> g_flags, g_segx, g_segoff, g_store, g_bitmap, hball_off;
+    std::vector<uint64_t> g_store_words;
+    size_t total = 0;
+};
 
-// Launches the sweep (and its set-up kernels) on stream; returns a GC_* code.
-int launch_sweep(const HostProblem& p, const gc_plan_t& plan, const SweepLayout& L,
-                 uint32_t* d_out, uint64_t capacity, gc_stats* d_stats, void* workspace,
+// Splits the SMs into groups (ngroups <= 0: one per job, up to the SM count),
+// assigns jobs to groups (longest first) and lays out the workspace.
+bool batch_layout(const BatchJob* jobs, int njobs, int ngroups, BatchLayout* L, std::string* why);
+
+// Launches the batched sweep (descriptor copies, set-up kernels, the
+// cooperative sweep) on stream; returns a GC_* code.
+int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
                  cudaStream_t stream, std::string* why);
 
 // Step launchers (gc_steps.cu); each returns a GC_* code.

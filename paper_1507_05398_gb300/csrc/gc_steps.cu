@@ -96,7 +96,7 @@ struct StepSmem {
     __align__(16) uint32_t off[kStepChunk];
     __align__(16) uint32_t acc[kStepChunk];
     __align__(16) uint32_t tile[kStepChunk * 4];
-    uint32_t M[kResolveBlock][kResolveWords];
+    uint32_t M[kResolveWords][kResolveBlock];
     uint8_t dead[kStepChunk];
     BlockScratch bs;
 };

@@ -1,58 +1,80 @@
-// gc_sweep.cu -- the persistent windowed sweep: the whole ordered greedy
-// construction of Section 3 in one cooperative launch.
+// gc_sweep.cu -- the persistent windowed sweep: the ordered greedy
+// construction of Section 3 for one code or a batch of codes in one
+// cooperative launch.
 //
-// The rank space is cut into windows of W consecutive ranks.  For window t:
-//  1. (all CTAs, in parallel) every candidate of the window is generated from
-//     its rank (Section 4.2 orders, closed form) and tested against the code
-//     committed before the window:
-//       distance strategy: popcount(x ^ c) >= d against every codeword, most
-//         recent first, in shared-memory tiles with warp-wide early exit
-//         (Sections 4.1, 5.2);
+// The CTAs (one per SM) are split into groups; each group sweeps its own
+// list of jobs (codes) one after the other.  For one job the rank space is
+// cut into windows of W consecutive ranks, and for window t:
+//  1. (all CTAs of the group, in parallel) every candidate of the window is
+//     generated from its rank (Section 4.2 orders, closed form) and tested
+//     against the code committed before the window:
+//       distance strategy: popcount(x ^ c) >= d against every codeword,
+//         most recent first, from shared memory, with warp-wide early exit
+//         (Sections 4.1, 5.2); first every warp scans the newest codewords
+//         for its own candidates, then the few candidates left are scanned
+//         against the rest with the codeword range split across warps;
 //       bitmap strategy: one bit lookup in the exclusion bitmap, which holds
 //         the radius-(d-1) balls of every codeword accepted two or more
 //         windows ago, plus the distance test against the previous window's
-//         accepts, whose balls are being marked meanwhile.
-//     Survivors are written, in rank order, to a per-CTA segment.
-//  2. one grid-wide barrier.
-//  3. (every CTA, redundantly and identically) the survivors of the window are
+//         accepts, whose balls the group marks meanwhile.
+//     Survivors are written, in rank order, to the CTA's segment, and the CTA
+//     publishes (sequence number, count) in its flag word.
+//  2. each CTA waits until every flag of its group carries the window's
+//     sequence number (acquire loads, bounded wait).
+//  3. (every CTA of the group, redundantly and identically) the survivors are
 //     gathered in rank order and resolved in order (block_resolve), which
 //     reproduces the serial decisions; the accepts are appended to the code.
-//     Every CTA keeps its own copy of the new accepts, so no second barrier is
-//     needed before the next window.
-// The window size adapts so that about `target` candidates survive step 1;
-// if more than kSurvCap survive, the window is cut after the kSurvCap-th
-// survivor and the next window starts right after it.
-#include <cooperative_groups.h>
-
+//     Every CTA keeps its own copy of the accepts, so no second wait is needed.
+// The window size adapts so that about `target` candidates survive step 1; if
+// more than kSurvCap survive, the window is cut after the kSurvCap-th one.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "gc_block.cuh"
 #include "gc_internal.h"
 
 namespace gc {
 
-constexpr int kChunk = 4096;    // candidates per CTA per window
-constexpr int kSurvCap = 4096;  // survivors resolved per window
-constexpr int kMaxGrid = 1024;  // survivor-count prefix is one block scan
+constexpr int kChunk = 4096;       // candidates per CTA per window
+constexpr int kSurvCap = 4096;     // survivors resolved per window
+constexpr int kMaxGroupCtas = 1024;
+constexpr int kMinGroup = 8;       // CTAs of the smallest group when sizes follow cost
 enum : int { kStratDistance = 1, kStratBitmap = 2 };
 
-struct SweepArgs {
+// One code to generate (device-side descriptor).
+struct JobDesc {
     Order ord;
     int d;
     int strategy;
     uint32_t* out;
     uint64_t cap;
     gc_stats* stats;
-    unsigned* bar;
-    uint32_t* seg_cnt;   // [2][G]
-    uint32_t* seg_x;     // [2][G][kChunk]
-    uint32_t* seg_off;   // [2][G][kChunk]
-    uint32_t* store;     // distance strategy: code beyond the shared cache
-    uint64_t store_words;
-    uint32_t* bitmap;    // bitmap strategy: 2^n bits, vector-indexed
     const uint32_t* hball;
     uint32_t hball_len;
     uint32_t wmin, wmax, target;
+};
+
+// A group of CTAs and the scratch it owns.
+struct GroupDesc {
+    int first_cta, ncta;
+    int job_begin, job_end;       // range of job_order
+    unsigned long long* flags;    // [2][ncta]: (sequence << 32) | survivor count
+    uint32_t* seg_x;              // [2][ncta][kChunk]
+    uint32_t* seg_off;            // [2][ncta][kChunk]
+    uint32_t* store;              // distance jobs: code beyond the shared cache
+    uint64_t store_words;
+    uint32_t* bitmap;             // bitmap jobs: 2^n bits, vector-indexed
+};
+
+struct BatchArgs {
+    const JobDesc* jobs;
+    const int* job_order;
+    const GroupDesc* groups;
+    int ngroups;
+    unsigned* err;
     uint32_t cache_words;
     long long timeout_cycles;
 };
@@ -66,9 +88,13 @@ struct __align__(16) SweepSmem {
     __align__(16) uint32_t accA[kSurvCap];
     __align__(16) uint32_t accB[kSurvCap];
     __align__(16) uint32_t acc_off[kSurvCap];
-    uint32_t M[kResolveBlock][kResolveWords];
-    uint32_t pref[kMaxGrid + 1];
+    uint32_t M[kResolveWords][kResolveBlock];
+    uint32_t pref[kMaxGroupCtas + 1];
     uint8_t dead[kChunk];
+    JobDesc job;
+    GroupDesc grp;
+    unsigned long long phase[8];  // phase timers (thread 0 of the group's first CTA)
+    long long tprev;
     BlockScratch bs;
 };
 
@@ -79,17 +105,17 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(BlockScratch& bs, uint3
     uint32_t incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(kFull, incl, o);
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += t;
     }
     if (lane == 31) bs.warp_sum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = bs.warp_sum[lane];
+        const uint32_t w = bs.warp_sum[lane];
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(kFull, wi, o);
+            const uint32_t t = __shfl_up_sync(kFull, wi, o);
             if (lane >= o) wi += t;
         }
         bs.warp_sum[lane] = wi - w;
@@ -102,202 +128,349 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(BlockScratch& bs, uint3
     return ex;
 }
 
-__global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant__ SweepArgs a) {
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// CTA-wide.  Publishes this CTA's count for sequence number seq and waits
+// until every CTA of the group has published seq; then s.pref holds the
+// exclusive prefix of the counts and the total is returned.  Bounded: on
+// timeout (or when another CTA reported one) sets *ok = false.
+__device__ uint32_t group_exchange(SweepSmem& s, unsigned long long* flags, int lb, int gsize,
+                                   uint32_t seq, uint32_t count, unsigned* err, long long timeout,
+                                   bool* ok) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        st_release_u64(flags + lb, ((unsigned long long)seq << 32) | count);
+    uint32_t v = 0;
+    bool fine = true;
+    if ((int)threadIdx.x < gsize) {
+        const long long t0 = clock64();
+        for (;;) {
+            const unsigned long long f = ld_acquire_u64(flags + threadIdx.x);
+            if ((uint32_t)(f >> 32) == seq) {
+                v = (uint32_t)f;
+                break;
+            }
+            if (ld_acquire_gpu(err) != 0u) { fine = false; break; }
+            if (clock64() - t0 > timeout) {
+                atomicExch(err, 1u);
+                fine = false;
+                break;
+            }
+        }
+    }
+    if (threadIdx.x == 0) s.bs.flag_any = 1u;
+    __syncthreads();
+    if (!fine) s.bs.flag_any = 0u;
+    uint32_t total = 0;
+    const uint32_t ex = block_exclusive_scan(s.bs, v, &total);  // has barriers
+    if ((int)threadIdx.x < gsize) s.pref[threadIdx.x] = ex;
+    if (threadIdx.x == 0) s.pref[gsize] = total;
+    *ok = s.bs.flag_any != 0u;
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     SweepSmem& s = *reinterpret_cast<SweepSmem*>(smem_raw);
     uint32_t* cache = reinterpret_cast<uint32_t*>(smem_raw + sizeof(SweepSmem));
     const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
-    const uint32_t G = gridDim.x, b = blockIdx.x;
-    const Order& o = a.ord;
-    const int d = a.d;
-    const int n = o.n;
 
+    // which group this CTA belongs to
+    if (tid == 0) {
+        int g = 0;
+        while (g + 1 < a.ngroups && a.groups[g + 1].first_cta <= (int)blockIdx.x) ++g;
+        s.grp = a.groups[g];
+    }
     for (int q = tid; q < (kMaxN + 1) * (kMaxN + 1); q += kBlock) {
         const int p = q / (kMaxN + 1), k = q % (kMaxN + 1);
         uint64_t r = (k <= p) ? 1u : 0u;
         for (int i = 1; i <= k && k <= p; ++i) r = r * (uint64_t)(p - k + i) / (uint64_t)i;
         s.C[p][k] = (uint32_t)r;
     }
-    {
-        const int nl = n < 5 ? n : 5;
-        for (int q = tid; q < 8 * 32; q += kBlock) {
-            const int r = q / 32, c = q % 32;
-            uint32_t m = 0;
-            for (int y = 0; y < (1 << nl); ++y)
-                if (__popc((unsigned)(y ^ c)) <= r) m |= 1u << y;
-            s.lowball[r][c] = m;
-        }
-    }
     __syncthreads();
+    const GroupDesc& grp = s.grp;
+    const int lb = (int)blockIdx.x - grp.first_cta;
+    const int G = grp.ncta;
     const uint32_t(*C)[kMaxN + 1] = s.C;
-
-    uint64_t R0 = 0, K = 0, Kprev = 0;
-    uint32_t W = a.wmin;
-    uint32_t* cur = s.accA;
-    uint32_t* prev = s.accB;
-    uint32_t nprev = 0;
-    unsigned gen = 0;
-    int par = 0;
-    uint64_t my_tests = 0, my_marks = 0, dense = 0, resolve_tests = 0;
-    uint64_t windows = 0, surv_total = 0;
-
-    while (R0 < o.N) {
-        const uint64_t span = min((uint64_t)W, o.N - R0);
-        const uint64_t chunk = (span + G - 1) / G;
-        const uint64_t c0 = min(R0 + (uint64_t)b * chunk, R0 + span);
-        const uint64_t c1 = min(c0 + chunk, R0 + span);
-
-        // bitmap strategy: this CTA's share of the previous window's ball marks
-        if (a.strategy == kStratBitmap && nprev > 0) {
-            const uint64_t total = (uint64_t)nprev * a.hball_len;
-            const uint64_t per = (total + G - 1) / G;
-            const uint64_t q0 = min((uint64_t)b * per, total), q1 = min(q0 + per, total);
-            for (uint64_t q = q0 + tid; q < q1; q += kBlock) {
-                const uint32_t i = (uint32_t)(q / a.hball_len);
-                const uint32_t j = (uint32_t)(q - (uint64_t)i * a.hball_len);
-                const uint32_t c = prev[i];
-                const uint32_t e = __ldg(a.hball + j);
-                const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
-                uint32_t mask = s.lowball[e & 7u][c & 31u];
-                // only ranks after c matter; skip words wholly before it
-                if (o.ord == kLex) {
-                    if (word < cw) continue;
-                    if (word == cw) mask &= ~((2u << (c & 31u)) - 1u);
-                } else if (o.ord == kGray) {
-                    if (gray_inverse(word) < gray_inverse(cw)) continue;
-                }
-                if (mask) {
-                    atomicOr(a.bitmap + word, mask);
-                    ++my_marks;
-                }
-            }
+    const bool timing = (lb == 0 && tid == 0);
+    uint32_t seq = 0;
+    bool ok = true;
+    // every job's statistics start at zero (ordered before any other CTA's
+    // update by the first group exchange)
+    if (lb == 0 && tid == 0)
+        for (int jq = grp.job_begin; jq < grp.job_end; ++jq) {
+            gc_stats* st = a.jobs[a.job_order[jq]].stats;
+            st->codewords = 0; st->candidates = 0; st->dense_tests = 0; st->executed_tests = 0;
+            st->marks = 0; st->windows = 0; st->survivors = 0; st->status = 0; st->strategy = 0;
+            for (int k = 0; k < 8; ++k) st->phase_cycles[k] = 0;
         }
 
-        // candidates of this CTA's chunk, in rank order
-        uint32_t na = 0;
-        for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
-            const uint64_t r = t0 + tid;
-            uint32_t x = 0;
-            bool keep = false;
-            if (r < c1) {
-                keep = unrank(o, C, r, x);
-                if (keep && a.strategy == kStratBitmap)
-                    keep = !((ld_cg(a.bitmap + (x >> 5)) >> (x & 31u)) & 1u);
-            }
-            na = block_append(s.bs, keep, x, (uint32_t)(r - R0), s.list_x, s.list_off, na);
-        }
-
-        // test against the code committed before the window, most recent first
-        if (d >= 2) {
-            na = block_filter<false>(s.bs, s.list_x, s.list_off, s.dead, na, prev, 0, nprev, d,
-                                     my_tests);
-            if (a.strategy == kStratDistance) {
-                const uint32_t cached = (uint32_t)min(Kprev, (uint64_t)a.cache_words);
-                if (Kprev > a.cache_words)
-                    na = block_filter<true>(s.bs, s.list_x, s.list_off, s.dead, na, a.store,
-                                            a.cache_words, (uint32_t)Kprev, d, my_tests);
-                na = block_filter<false>(s.bs, s.list_x, s.list_off, s.dead, na, cache, 0, cached,
-                                         d, my_tests);
-            }
-        }
-
-        // publish this CTA's survivors
+    for (int jq = grp.job_begin; jq < grp.job_end && ok; ++jq) {
+        if (tid == 0) s.job = a.jobs[a.job_order[jq]];
+        __syncthreads();
+        const JobDesc& job = s.job;
+        const Order& o = job.ord;
+        const int d = job.d;
+        const int n = o.n;
         {
-            uint32_t* sx = a.seg_x + ((size_t)par * G + b) * kChunk;
-            uint32_t* so = a.seg_off + ((size_t)par * G + b) * kChunk;
-            for (uint32_t i = tid; i < na; i += kBlock) {
-                sx[i] = s.list_x[i];
-                so[i] = s.list_off[i];
-            }
-            if (tid == 0) a.seg_cnt[par * G + b] = na;
-        }
-        if (!grid_sync(a.bar, G, gen, a.timeout_cycles, s.bs.flag_any)) break;
-
-        // gather every CTA's survivors in CTA (= rank) order
-        uint32_t S = 0;
-        {
-            const uint32_t v = (uint32_t)tid < G ? ld_cg(a.seg_cnt + par * G + tid) : 0u;
-            const uint32_t ex = block_exclusive_scan(s.bs, v, &S);
-            if ((uint32_t)tid < G) s.pref[tid] = ex;
-            if (tid == 0) s.pref[G] = S;
-        }
-        __syncthreads();
-        const uint32_t Suse = min(S, (uint32_t)kSurvCap);
-        for (uint32_t g = warp; g < G; g += kWarps) {
-            const uint32_t p0 = s.pref[g];
-            if (p0 >= Suse) continue;
-            const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
-            const uint32_t* gx = a.seg_x + ((size_t)par * G + g) * kChunk;
-            const uint32_t* go = a.seg_off + ((size_t)par * G + g) * kChunk;
-            for (uint32_t i = lane; i < cnt; i += 32) {
-                s.list_x[p0 + i] = ld_cg(gx + i);
-                s.list_off[p0 + i] = ld_cg(go + i);
+            const int nl = n < 5 ? n : 5;
+            for (int q = tid; q < 8 * 32; q += kBlock) {
+                const int r = q / 32, c = q % 32;
+                uint32_t m = 0;
+                for (int y = 0; y < (1 << nl); ++y)
+                    if (__popc((unsigned)(y ^ c)) <= r) m |= 1u << y;
+                s.lowball[r][c] = m;
             }
         }
-        __syncthreads();
-        const uint64_t Rnext = (S > (uint32_t)kSurvCap) ? R0 + s.list_off[kSurvCap - 1] + 1
-                                                        : R0 + span;
-
-        // resolve in order; identical in every CTA
-        uint64_t rt = 0;
-        const uint32_t nacc = block_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                            s.acc_off, s.M, rt);
-        if (b == 0) resolve_tests += rt;
-
-        // commit
-        if (b == 0) {
-            for (uint32_t i = tid; i < nacc; i += kBlock) {
-                const uint64_t pos = K + i;
-                if (pos < a.cap) a.out[pos] = cur[i];
-                if (!o.filter) dense += o.N - 1 - (R0 + s.acc_off[i]);
-            }
+        // job start: clear this CTA's share of the bitmap
+        if (job.strategy == kStratBitmap) {
+            const uint64_t words = ((1ull << n) + 31) / 32;
+            const uint64_t per = (words + G - 1) / G;
+            const uint64_t w0 = min((uint64_t)lb * per, words), w1 = min(w0 + per, words);
+            for (uint64_t w = w0 + tid; w < w1; w += kBlock) grp.bitmap[w] = 0u;
         }
-        if (a.strategy == kStratDistance) {
-            for (uint32_t i = tid; i < nacc; i += kBlock) {
-                const uint64_t pos = K + i;
-                if (b == 0 && pos < a.store_words) a.store[pos] = cur[i];
-                if (pos < a.cache_words) cache[pos] = cur[i];
-            }
-        }
-        ++windows;
-        surv_total += Suse;
-        if (S > 2u * a.target)
-            W = max(W / 2u, a.wmin);
-        else if (S < a.target / 2u)
-            W = min(W * 2u, a.wmax);
-        Kprev = K;
-        K += nacc;
-        uint32_t* t = cur;
-        cur = prev;
-        prev = t;
-        nprev = nacc;
-        R0 = Rnext;
-        par ^= 1;
-        __syncthreads();
-    }
+        group_exchange(s, grp.flags + (size_t)(seq & 1) * G, lb, G, seq, 0, a.err,
+                       a.timeout_cycles, &ok);
+        ++seq;
+        if (!ok) break;
 
-    // statistics: warp-reduce then one atomic per warp
-    uint64_t t = my_tests + resolve_tests, m = my_marks, dn = dense;
+        uint64_t R0 = 0, K = 0, Kprev = 0;
+        uint32_t W = job.wmin;
+        uint32_t* cur = s.accA;
+        uint32_t* prev = s.accB;
+        uint32_t nprev = 0;
+        uint64_t my_tests = 0, my_marks = 0, dense = 0, resolve_tests = 0;
+        uint64_t windows = 0, surv_total = 0;
+        if (timing)
+            for (int k = 0; k < 8; ++k) s.phase[k] = 0;
+        // adds the cycles since the last mark to phase k (first CTA, thread 0)
+        auto mark_phase = [&](int k) {
+            if (timing) {
+                const long long t = clock64();
+                s.phase[k] += (unsigned long long)(t - s.tprev);
+                s.tprev = t;
+            }
+        };
+
+        while (R0 < o.N) {
+            if (timing) s.tprev = clock64();
+            const uint64_t span = min((uint64_t)W, o.N - R0);
+            const uint64_t chunk = (span + G - 1) / G;
+            const uint64_t c0 = min(R0 + (uint64_t)lb * chunk, R0 + span);
+            const uint64_t c1 = min(c0 + chunk, R0 + span);
+
+            // bitmap strategy: this CTA's share of the previous window's marks
+            if (job.strategy == kStratBitmap && nprev > 0) {
+                const uint32_t hl = job.hball_len;
+                const uint64_t total = (uint64_t)nprev * hl;
+                const uint64_t per = (total + G - 1) / G;
+                const uint64_t q0 = min((uint64_t)lb * per, total), q1 = min(q0 + per, total);
+                // (i, j) = divmod(q, hl), advanced by kBlock without dividing
+                const uint64_t qs = q0 + tid;
+                uint32_t i = (uint32_t)(qs / hl), j = (uint32_t)(qs - (uint64_t)i * hl);
+                const uint32_t di = kBlock / hl, dj = kBlock - di * hl;
+                for (uint64_t q = qs; q < q1; q += kBlock) {
+                    const uint32_t c = prev[i];
+                    const uint32_t e = __ldg(job.hball + j);
+                    const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
+                    uint32_t mask = s.lowball[e & 7u][c & 31u];
+                    bool skip = false;
+                    // only ranks after c matter; skip words wholly before it
+                    if (o.ord == kLex) {
+                        skip = word < cw;
+                        if (word == cw) mask &= ~((2u << (c & 31u)) - 1u);
+                    } else if (o.ord == kGray) {
+                        skip = gray_inverse(word) < gray_inverse(cw);
+                    }
+                    if (!skip && mask) {
+                        atomicOr(grp.bitmap + word, mask);
+                        ++my_marks;
+                    }
+                    i += di;
+                    j += dj;
+                    if (j >= hl) {
+                        j -= hl;
+                        ++i;
+                    }
+                }
+            }
+            mark_phase(0);
+            // candidates of this CTA's chunk, in rank order
+            uint32_t na = 0;
+            for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
+                const uint64_t r = t0 + tid;
+                uint32_t x = 0;
+                bool keep = false;
+                if (r < c1) {
+                    keep = unrank(o, C, r, x);
+                    if (keep && job.strategy == kStratBitmap)
+                        keep = !((ld_cg(grp.bitmap + (x >> 5)) >> (x & 31u)) & 1u);
+                }
+                na = block_append(s.bs, keep, x, (uint32_t)(r - R0), s.list_x, s.list_off, na);
+            }
+
+            // test against the code committed before the window, newest first:
+            // prev (the previous window's accepts), then for the distance
+            // strategy the older code (global store above the cache, then the
+            // cache)
+            mark_phase(1);
+            if (d >= 2 && na > 0) {
+                // the committed code in newest-first order: prev (the previous
+                // window's accepts), then for the distance strategy the global
+                // store above the shared cache, then the cache.  It is scanned
+                // in slices of growing length; after each slice the survivors
+                // are compacted so lanes stay busy with live candidates.
+                const uint32_t ncached =
+                    job.strategy == kStratDistance ? (uint32_t)min(Kprev, (uint64_t)a.cache_words) : 0u;
+                const uint32_t nglob = (job.strategy == kStratDistance && Kprev > a.cache_words)
+                                           ? (uint32_t)(Kprev - a.cache_words) : 0u;
+                const uint32_t total = nprev + nglob + ncached;
+                uint32_t u = 0;
+                while (na > 0 && u < total) {
+                    // short list: the rest in one slice (block_test splits the
+                    // codeword range across warps); else 16, then up to 256
+                    uint32_t u1 = total;
+                    if (na > 8u * 32u) u1 = min(total, u < 16u ? 16u : (u < 256u ? 256u : total));
+                    for (uint32_t i = tid; i < na; i += kBlock) s.dead[i] = 0;
+                    __syncthreads();
+                    // prev: unified [0, nprev) -> prev[nprev-1 .. 0]
+                    if (u < nprev) {
+                        const uint32_t hi = min(u1, nprev);
+                        block_test<false>(s.list_x, na, s.dead, prev, nprev - hi, nprev - u, d, my_tests);
+                    }
+                    // global store: unified [nprev, nprev+nglob) -> store[Kprev-1 ..]
+                    if (nglob && u1 > nprev && u < nprev + nglob) {
+                        const uint32_t lo = max(u, nprev) - nprev, hi = min(u1, nprev + nglob) - nprev;
+                        block_test<true>(s.list_x, na, s.dead, grp.store, (uint32_t)Kprev - hi,
+                                         (uint32_t)Kprev - lo, d, my_tests);
+                    }
+                    // cache: unified [nprev+nglob, total) -> cache[ncached-1 .. 0]
+                    if (ncached && u1 > nprev + nglob) {
+                        const uint32_t base = nprev + nglob;
+                        const uint32_t lo = max(u, base) - base, hi = u1 - base;
+                        block_test<false>(s.list_x, na, s.dead, cache, ncached - hi, ncached - lo, d,
+                                          my_tests);
+                    }
+                    __syncthreads();
+                    na = block_compact(s.bs, s.list_x, s.list_off, s.dead, na);
+                    u = u1;
+                    if (u == 16u || u1 == total) mark_phase(2);
+                }
+            }
+            mark_phase(3);
+
+            // publish this CTA's survivors and wait for the group
+            {
+                const int par = seq & 1;
+                uint32_t* sx = grp.seg_x + ((size_t)par * G + lb) * kChunk;
+                uint32_t* so = grp.seg_off + ((size_t)par * G + lb) * kChunk;
+                for (uint32_t i = tid; i < na; i += kBlock) {
+                    sx[i] = s.list_x[i];
+                    so[i] = s.list_off[i];
+                }
+            }
+            const int par = seq & 1;
+            const uint32_t S = group_exchange(s, grp.flags + (size_t)par * G, lb, G, seq, na,
+                                              a.err, a.timeout_cycles, &ok);
+            ++seq;
+            if (!ok) break;
+            mark_phase(4);
+
+            // gather every CTA's survivors in CTA (= rank) order
+            const uint32_t Suse = min(S, (uint32_t)kSurvCap);
+            for (int g = warp; g < G; g += kWarps) {
+                const uint32_t p0 = s.pref[g];
+                if (p0 >= Suse) continue;
+                const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
+                const uint32_t* gx = grp.seg_x + ((size_t)par * G + g) * kChunk;
+                const uint32_t* go = grp.seg_off + ((size_t)par * G + g) * kChunk;
+                for (uint32_t i = lane; i < cnt; i += 32) {
+                    s.list_x[p0 + i] = ld_cg(gx + i);
+                    s.list_off[p0 + i] = ld_cg(go + i);
+                }
+            }
+            __syncthreads();
+            const uint64_t Rnext = (S > (uint32_t)kSurvCap) ? R0 + s.list_off[kSurvCap - 1] + 1
+                                                            : R0 + span;
+            mark_phase(5);
+
+            // resolve in order; identical in every CTA of the group
+            uint64_t rt = 0;
+            const uint32_t nacc = block_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
+                                                s.acc_off, s.M, rt);
+            if (lb == 0) resolve_tests += rt;
+            mark_phase(6);
+
+            // commit
+            if (lb == 0) {
+                for (uint32_t i = tid; i < nacc; i += kBlock) {
+                    const uint64_t pos = K + i;
+                    if (pos < job.cap) job.out[pos] = cur[i];
+                    if (!o.filter) dense += o.N - 1 - (R0 + s.acc_off[i]);
+                }
+            }
+            if (job.strategy == kStratDistance) {
+                for (uint32_t i = tid; i < nacc; i += kBlock) {
+                    const uint64_t pos = K + i;
+                    if (lb == 0 && pos < grp.store_words) grp.store[pos] = cur[i];
+                    if (pos < a.cache_words) cache[pos] = cur[i];
+                }
+            }
+            ++windows;
+            surv_total += Suse;
+            if (S > 2u * job.target)
+                W = max(W / 2u, job.wmin);
+            else if (S < job.target / 2u)
+                W = min(W * 2u, job.wmax);
+            Kprev = K;
+            K += nacc;
+            uint32_t* t = cur;
+            cur = prev;
+            prev = t;
+            nprev = nacc;
+            R0 = Rnext;
+            __syncthreads();
+            mark_phase(7);
+        }
+
+        // statistics: warp-reduce then one atomic per warp
+        uint64_t tt = my_tests + resolve_tests, m = my_marks, dn = dense;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        t += __shfl_down_sync(kFull, t, off);
-        m += __shfl_down_sync(kFull, m, off);
-        dn += __shfl_down_sync(kFull, dn, off);
-    }
-    if (lane == 0) {
-        if (t) atomicAdd((unsigned long long*)&a.stats->executed_tests, (unsigned long long)t);
-        if (m) atomicAdd((unsigned long long*)&a.stats->marks, (unsigned long long)m);
-        if (dn) atomicAdd((unsigned long long*)&a.stats->dense_tests, (unsigned long long)dn);
-    }
-    if (tid == 0) {
-        if (ld_acquire_gpu(&a.bar[2]) != 0u) atomicMax((int*)&a.stats->status, (int)GC_ERR_TIMEOUT);
-        if (b == 0) {
-            a.stats->codewords = K;
-            a.stats->candidates = o.N;
-            a.stats->windows = windows;
-            a.stats->survivors = surv_total;
-            a.stats->strategy = a.strategy;
+        for (int off = 16; off > 0; off >>= 1) {
+            tt += __shfl_down_sync(kFull, tt, off);
+            m += __shfl_down_sync(kFull, m, off);
+            dn += __shfl_down_sync(kFull, dn, off);
         }
+        if (lane == 0) {
+            if (tt) atomicAdd((unsigned long long*)&job.stats->executed_tests, (unsigned long long)tt);
+            if (m) atomicAdd((unsigned long long*)&job.stats->marks, (unsigned long long)m);
+            if (dn) atomicAdd((unsigned long long*)&job.stats->dense_tests, (unsigned long long)dn);
+        }
+        if (tid == 0 && lb == 0) {
+            job.stats->codewords = K;
+            job.stats->candidates = o.N;
+            job.stats->windows = windows;
+            job.stats->survivors = surv_total;
+            job.stats->strategy = job.strategy;
+            for (int k = 0; k < 8; ++k) job.stats->phase_cycles[k] = s.phase[k];
+        }
+        // the next job reuses the statistics-free scratch; make sure every CTA
+        // of the group is done with this job's shared state first
+        __syncthreads();
+    }
+    if (tid == 0 && (!ok || ld_acquire_gpu(a.err) != 0u)) {
+        // report on every job this group owns (the failing one is among them)
+        for (int jq = grp.job_begin; jq < grp.job_end; ++jq)
+            atomicMax((int*)&a.jobs[a.job_order[jq]].stats->status, (int)GC_ERR_TIMEOUT);
     }
 }
 
@@ -340,9 +513,34 @@ uint64_t high_ball_len(int n, int d) {
     return len;
 }
 
+// ------------------------------------------------------------------ host side
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-bool sweep_layout(const HostProblem& p, const gc_plan_t& plan, SweepLayout* L, std::string* why) {
+static Order make_order_host(const HostProblem& p) {
+    Order o{};
+    o.n = p.n;
+    o.ord = p.ord;
+    o.w = p.w;
+    o.filter = p.filter;
+    o.N = p.N;
+    uint64_t c = 0;
+    for (int k = 0; k <= kMaxN + 1; ++k) {
+        o.cum[k] = c;
+        if (k <= p.n) c += binom64(p.n, k);
+    }
+    return o;
+}
+
+// Rough device cost of one job, used to balance jobs over groups.
+static double job_cost(const HostProblem& p, int strategy) {
+    const double N = (double)p.valid;
+    const double C = std::max(1.0, 0.5 * (double)p.bound);
+    if (strategy == GC_STRATEGY_BITMAP) return N + 8.0 * C * (double)high_ball_len(p.n, p.d);
+    return N * 32.0 + C * C;
+}
+
+bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout* L,
+                  std::string* why) {
     int dev = 0, sms = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -351,115 +549,233 @@ bool sweep_layout(const HostProblem& p, const gc_plan_t& plan, SweepLayout* L, s
         *why = "cannot query the CUDA device";
         return false;
     }
-    int grid = plan.grid > 0 ? plan.grid : sms;
-    if (grid > sms) grid = sms;  // one CTA per SM (the kernel needs most of an SM)
-    if (grid > kMaxGrid) grid = kMaxGrid;
-    L->grid = grid;
+    if (njobs < 1) {
+        *why = "no jobs";
+        return false;
+    }
     const size_t base = sizeof(SweepSmem);
     if ((size_t)optin < base + 16) {
         *why = "not enough shared memory per block";
         return false;
     }
-    uint32_t cache = 0;
-    if (plan.strategy == GC_STRATEGY_DISTANCE) {
-        uint64_t room = ((size_t)optin - base) / 4;
-        cache = (uint32_t)std::min<uint64_t>(room & ~(uint64_t)31, p.bound);
-        cache = (cache + 31) & ~31u;
-        if ((size_t)cache * 4 + base > (size_t)optin) cache -= 32;
-    }
+    int grid = sms;
+    for (int j = 0; j < njobs; ++j)
+        if (jobs[j].plan.grid > 0) grid = std::min(grid, jobs[j].plan.grid);
+    int ng = ngroups_req > 0 ? ngroups_req : std::min(njobs, grid);
+    ng = std::max(1, std::min(ng, std::min(njobs, grid)));
+    L->grid = grid;
+    L->ngroups = ng;
+    // shared-memory code cache for distance jobs
+    uint64_t need_cache = 0;
+    for (int j = 0; j < njobs; ++j)
+        if (jobs[j].plan.strategy == GC_STRATEGY_DISTANCE)
+            need_cache = std::max<uint64_t>(need_cache, jobs[j].p.bound);
+    uint64_t room = (((size_t)optin - base) / 4) & ~(uint64_t)31;
+    uint32_t cache = (uint32_t)std::min<uint64_t>(room, (need_cache + 31) & ~(uint64_t)31);
     L->cache_words = cache;
     L->smem_bytes = base + (size_t)cache * 4;
-    L->store_words = (plan.strategy == GC_STRATEGY_DISTANCE && p.bound > cache) ? p.bound : 0;
-    if (L->store_words > 0xffffffffull) {
-        *why = "code too large for the distance strategy";
-        return false;
+    std::vector<double> cost(njobs);
+    for (int j = 0; j < njobs; ++j) cost[j] = job_cost(jobs[j].p, jobs[j].plan.strategy);
+    L->first_cta.assign(ng, 0);
+    L->ncta.assign(ng, 0);
+    std::vector<std::vector<int>> per(ng);
+    if (ng == njobs && ng > 1) {
+        // one job per group: CTAs in proportion to the job's estimated work,
+        // at least kMinGroup (or an equal share if the SMs are too few)
+        const int minc = std::max(1, std::min(kMinGroup, grid / ng));
+        double total = 0;
+        for (double c : cost) total += c;
+        int left = grid - minc * ng;
+        std::vector<int> extra(ng, 0);
+        int given = 0;
+        for (int g = 0; g < ng; ++g) {
+            extra[g] = (int)std::floor(left * cost[g] / std::max(total, 1e-30));
+            given += extra[g];
+        }
+        for (int g = 0; given < left; g = (g + 1) % ng, ++given) extra[g] += 1;
+        int at = 0;
+        for (int g = 0; g < ng; ++g) {
+            L->first_cta[g] = at;
+            L->ncta[g] = minc + extra[g];
+            at += L->ncta[g];
+            per[g].push_back(g);
+        }
+    } else {
+        // equal CTA counts; jobs longest first onto the least-loaded group
+        for (int g = 0; g < ng; ++g) {
+            L->first_cta[g] = g * grid / ng;
+            L->ncta[g] = (g + 1) * grid / ng - L->first_cta[g];
+        }
+        std::vector<int> idx(njobs);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<double> load(ng, 0.0);
+        for (int j : idx) {
+            const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            per[g].push_back(j);
+            load[g] += cost[j] / std::max(1, L->ncta[g]);
+        }
     }
+    for (int g = 0; g < ng; ++g)
+        if (L->ncta[g] > kMaxGroupCtas || L->ncta[g] < 1) {
+            *why = "bad group size";
+            return false;
+        }
+    L->job_order.clear();
+    L->job_begin.assign(ng, 0);
+    L->job_end.assign(ng, 0);
+    for (int g = 0; g < ng; ++g) {
+        // keep each group's jobs in submission order
+        std::sort(per[g].begin(), per[g].end());
+        L->job_begin[g] = (int)L->job_order.size();
+        for (int j : per[g]) L->job_order.push_back(j);
+        L->job_end[g] = (int)L->job_order.size();
+    }
+    // workspace
     size_t off = 0;
-    L->off_bar = off;     off += align_up(64);
-    L->off_segcnt = off;  off += align_up(sizeof(uint32_t) * 2 * grid);
-    L->off_segx = off;    off += align_up(sizeof(uint32_t) * 2 * (size_t)grid * kChunk);
-    L->off_segoff = off;  off += align_up(sizeof(uint32_t) * 2 * (size_t)grid * kChunk);
-    L->off_store = off;   off += align_up(sizeof(uint32_t) * L->store_words);
-    L->off_bitmap = off;
-    if (plan.strategy == GC_STRATEGY_BITMAP) {
-        off += align_up(((1ull << p.n) + 31) / 32 * 4);
+    L->off_err = off;        off += align_up(256);
+    L->off_jobs = off;       off += align_up(sizeof(JobDesc) * njobs);
+    L->off_order = off;      off += align_up(sizeof(int) * njobs);
+    L->off_groups = off;     off += align_up(sizeof(GroupDesc) * ng);
+    L->g_flags.assign(ng, 0); L->g_segx.assign(ng, 0); L->g_segoff.assign(ng, 0);
+    L->g_store.assign(ng, 0); L->g_store_words.assign(ng, 0); L->g_bitmap.assign(ng, 0);
+    for (int g = 0; g < ng; ++g) {
+        uint64_t store = 0, bits = 0;
+        for (int q = L->job_begin[g]; q < L->job_end[g]; ++q) {
+            const BatchJob& J = jobs[L->job_order[q]];
+            if (J.plan.strategy == GC_STRATEGY_DISTANCE && J.p.bound > cache)
+                store = std::max<uint64_t>(store, J.p.bound);
+            if (J.plan.strategy == GC_STRATEGY_BITMAP)
+                bits = std::max<uint64_t>(bits, 1ull << J.p.n);
+        }
+        if (store > 0xffffffffull) {
+            *why = "code too large for the distance strategy";
+            return false;
+        }
+        const int G = L->ncta[g];
+        // one spare flag pair per group (used only by the wait-fault injection)
+        L->g_flags[g] = off;  off += align_up(sizeof(unsigned long long) * 2 * (G + 1));
+        L->g_segx[g] = off;   off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
+        L->g_segoff[g] = off; off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
+        L->g_store[g] = off;  off += align_up(sizeof(uint32_t) * store);
+        L->g_store_words[g] = store;
+        L->g_bitmap[g] = off; off += align_up((bits + 31) / 32 * 4);
     }
-    L->off_hball = off;
-    if (plan.strategy == GC_STRATEGY_BITMAP) off += align_up(4 * high_ball_len(p.n, p.d));
+    // ball tables, one per distinct (n, d) among bitmap jobs
+    L->hball_off.assign(njobs, 0);
+    for (int j = 0; j < njobs; ++j) {
+        if (jobs[j].plan.strategy != GC_STRATEGY_BITMAP) continue;
+        int same = -1;
+        for (int i = 0; i < j; ++i)
+            if (jobs[i].plan.strategy == GC_STRATEGY_BITMAP && jobs[i].p.n == jobs[j].p.n &&
+                jobs[i].p.d == jobs[j].p.d) { same = i; break; }
+        if (same >= 0) { L->hball_off[j] = L->hball_off[same]; continue; }
+        L->hball_off[j] = off;
+        off += align_up(4 * high_ball_len(jobs[j].p.n, jobs[j].p.d));
+    }
     L->total = off;
     return true;
 }
 
-int launch_sweep(const HostProblem& p, const gc_plan_t& plan, const SweepLayout& L,
-                 uint32_t* d_out, uint64_t capacity, gc_stats* d_stats, void* workspace,
+int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
                  cudaStream_t stream, std::string* why) {
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    SweepArgs a{};
-    a.ord.n = p.n;
-    a.ord.ord = p.ord;
-    a.ord.w = p.w;
-    a.ord.filter = p.filter;
-    a.ord.N = p.N;
-    {
-        uint64_t c = 0;
-        for (int k = 0; k <= kMaxN + 1; ++k) {
-            a.ord.cum[k] = c;
-            if (k <= p.n) c += binom64(p.n, k);
-        }
+    // Host-side fault injection for tests of the failure path: GC_FAULT=wait
+    // makes group 0 wait for one CTA that does not exist, with a 0.2 s limit,
+    // so its bounded waits expire and every job reports GC_ERR_TIMEOUT.
+    const char* fault = std::getenv("GC_FAULT");
+    const bool inject_wait = fault && std::strcmp(fault, "wait") == 0;
+    std::vector<JobDesc> jd(njobs);
+    for (int j = 0; j < njobs; ++j) {
+        const BatchJob& J = jobs[j];
+        JobDesc& D = jd[j];
+        D.ord = make_order_host(J.p);
+        D.d = J.p.d;
+        D.strategy = J.plan.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
+        D.out = J.d_out;
+        D.cap = J.capacity;
+        D.stats = J.d_stats;
+        D.hball = D.strategy == kStratBitmap ? reinterpret_cast<const uint32_t*>(ws + L.hball_off[j])
+                                             : nullptr;
+        D.hball_len = D.strategy == kStratBitmap ? (uint32_t)high_ball_len(J.p.n, J.p.d) : 0u;
+        D.target = J.plan.survivor_target ? J.plan.survivor_target : 256;
+        // a window never holds more candidates than the group's chunks
+        int g = 0;
+        for (int q = 0; q < L.ngroups; ++q)
+            for (int i = L.job_begin[q]; i < L.job_end[q]; ++i)
+                if (L.job_order[i] == j) g = q;
+        const uint64_t wcap = (uint64_t)L.ncta[g] * kChunk;
+        D.wmax = (uint32_t)std::min<uint64_t>(J.plan.window_max ? J.plan.window_max : wcap, wcap);
+        D.wmin = std::max<uint32_t>(
+            1, std::min<uint32_t>(J.plan.window_min ? J.plan.window_min : 256, D.wmax));
     }
-    a.d = p.d;
-    a.strategy = plan.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
-    a.out = d_out;
-    a.cap = capacity;
-    a.stats = d_stats;
-    a.bar = reinterpret_cast<unsigned*>(ws + L.off_bar);
-    a.seg_cnt = reinterpret_cast<uint32_t*>(ws + L.off_segcnt);
-    a.seg_x = reinterpret_cast<uint32_t*>(ws + L.off_segx);
-    a.seg_off = reinterpret_cast<uint32_t*>(ws + L.off_segoff);
-    a.store = reinterpret_cast<uint32_t*>(ws + L.off_store);
-    a.store_words = L.store_words;
-    a.bitmap = reinterpret_cast<uint32_t*>(ws + L.off_bitmap);
-    a.hball = reinterpret_cast<const uint32_t*>(ws + L.off_hball);
-    a.hball_len = (uint32_t)high_ball_len(p.n, p.d);
-    a.target = plan.survivor_target ? plan.survivor_target : 256;
-    const uint64_t wcap = (uint64_t)L.grid * kChunk;
-    a.wmax = (uint32_t)std::min<uint64_t>(plan.window_max ? plan.window_max : wcap, wcap);
-    a.wmin = std::max<uint32_t>(1, std::min<uint32_t>(plan.window_min ? plan.window_min : 256, a.wmax));
-    a.cache_words = L.cache_words;
-    a.timeout_cycles = 20000000000ll;  // ~10 s at 2 GHz
-
+    std::vector<GroupDesc> gd(L.ngroups);
+    for (int g = 0; g < L.ngroups; ++g) {
+        GroupDesc& G = gd[g];
+        G.first_cta = L.first_cta[g];
+        G.ncta = L.ncta[g] + ((inject_wait && g == 0) ? 1 : 0);
+        G.job_begin = L.job_begin[g];
+        G.job_end = L.job_end[g];
+        G.flags = reinterpret_cast<unsigned long long*>(ws + L.g_flags[g]);
+        G.seg_x = reinterpret_cast<uint32_t*>(ws + L.g_segx[g]);
+        G.seg_off = reinterpret_cast<uint32_t*>(ws + L.g_segoff[g]);
+        G.store = reinterpret_cast<uint32_t*>(ws + L.g_store[g]);
+        G.store_words = L.g_store_words[g];
+        G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
+    }
     cudaError_t e;
-    if ((e = cudaMemsetAsync(ws + L.off_bar, 0, 64, stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(d_stats, 0, sizeof(gc_stats), stream)) != cudaSuccess) {
-        *why = cudaGetErrorString(e);
+    auto cuda_fail = [&](const char* what) {
+        *why = std::string(what) + ": " + cudaGetErrorString(e);
         return GC_ERR_CUDA;
+    };
+    // descriptors (pageable host memory: staged before the call returns)
+    if ((e = cudaMemcpyAsync(ws + L.off_jobs, jd.data(), sizeof(JobDesc) * njobs,
+                             cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail("job descriptors");
+    if ((e = cudaMemcpyAsync(ws + L.off_order, L.job_order.data(), sizeof(int) * njobs,
+                             cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail("job order");
+    if ((e = cudaMemcpyAsync(ws + L.off_groups, gd.data(), sizeof(GroupDesc) * L.ngroups,
+                             cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail("group descriptors");
+    if ((e = cudaMemsetAsync(ws + L.off_err, 0, 256, stream)) != cudaSuccess)
+        return cuda_fail("error word");
+    for (int g = 0; g < L.ngroups; ++g) {
+        // flags start at sequence 0xffffffff so no stale value matches
+        if ((e = cudaMemsetAsync(ws + L.g_flags[g], 0xff,
+                                 sizeof(unsigned long long) * 2 * (L.ncta[g] + 1), stream)) !=
+            cudaSuccess)
+            return cuda_fail("group flags");
     }
-    if (a.strategy == kStratBitmap) {
-        const size_t bytes = ((1ull << p.n) + 31) / 32 * 4;
-        if ((e = cudaMemsetAsync(a.bitmap, 0, bytes, stream)) != cudaSuccess) {
-            *why = cudaGetErrorString(e);
-            return GC_ERR_CUDA;
-        }
-        const int nh = p.n > 5 ? p.n - 5 : 0;
-        const int rc = launch_high_ball(nh, p.d - 1, const_cast<uint32_t*>(a.hball), a.hball_len,
-                                        stream);
+    for (int j = 0; j < njobs; ++j) {
+        if (jd[j].strategy != kStratBitmap) continue;
+        bool first = true;
+        for (int i = 0; i < j; ++i)
+            if (jd[i].strategy == kStratBitmap && L.hball_off[i] == L.hball_off[j]) first = false;
+        if (!first) continue;
+        const int nh = jobs[j].p.n > 5 ? jobs[j].p.n - 5 : 0;
+        const int rc = launch_high_ball(nh, jobs[j].p.d - 1, const_cast<uint32_t*>(jd[j].hball),
+                                        jd[j].hball_len, stream);
         if (rc) {
             *why = "ball table";
             return rc;
         }
     }
     if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)L.smem_bytes)) != cudaSuccess) {
-        *why = cudaGetErrorString(e);
-        return GC_ERR_CUDA;
-    }
+                                  (int)L.smem_bytes)) != cudaSuccess)
+        return cuda_fail("shared memory attribute");
+    BatchArgs a{};
+    a.jobs = reinterpret_cast<const JobDesc*>(ws + L.off_jobs);
+    a.job_order = reinterpret_cast<const int*>(ws + L.off_order);
+    a.groups = reinterpret_cast<const GroupDesc*>(ws + L.off_groups);
+    a.ngroups = L.ngroups;
+    a.err = reinterpret_cast<unsigned*>(ws + L.off_err);
+    a.cache_words = L.cache_words;
+    a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(L.grid), dim3(kBlock), args,
                                     L.smem_bytes, stream);
-    if (e != cudaSuccess) {
-        *why = std::string("sweep launch: ") + cudaGetErrorString(e);
-        return GC_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return cuda_fail("sweep launch");
     return GC_OK;
 }
 

@@ -22,6 +22,7 @@ __all__ = [
     "generate", "generate_async", "generate_host",
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
     "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
+    "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
 ]
 
 LEX, GRAY, GRLEX, GREVLEX = 0, 1, 2, 3
@@ -54,15 +55,24 @@ class Plan(ctypes.Structure):
                 ("survivor_target", ctypes.c_uint32)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("prob", Problem), ("strategy", ctypes.c_int), ("d_out", ctypes.c_void_p),
+                ("capacity", ctypes.c_uint64), ("d_stats", ctypes.c_void_p)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("codewords", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("dense_tests", ctypes.c_uint64), ("executed_tests", ctypes.c_uint64),
                 ("marks", ctypes.c_uint64), ("windows", ctypes.c_uint64),
                 ("survivors", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("strategy", ctypes.c_int32)]
+                ("strategy", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8)]
+
+    PHASES = ("mark", "generate", "test_new", "test_old", "wait", "gather", "resolve", "commit")
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_cycles"}
+        d["phase_cycles"] = dict(zip(self.PHASES, list(self.phase_cycles)))
+        return d
 
 
 _lock = threading.Lock()
@@ -88,6 +98,8 @@ _SIGS = {
     "gc_probe_test_rate": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "gc_generate_noalloc": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan), _vp, _u64, _vp,
                                    _vp]),
+    "gc_batch_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Job), _i32, _i32]),
+    "gc_batch_generate_async": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp]),
     "gc_noalloc_scratch_bytes": (ctypes.c_size_t, []),
 }
 
@@ -222,6 +234,73 @@ def generate_noalloc(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, stra
 
 def noalloc_scratch_bytes() -> int:
     return int(lib().gc_noalloc_scratch_bytes())
+
+
+_STRAT = {None: 0, "auto": 0, "distance": 1, "bitmap": 2}
+
+
+class BatchBuffers:
+    """Device buffers (outputs, stats, workspace) for a batch of problems.
+
+    problems: list of (n, d, ordering, weight[, strategy]).  Allocated once
+    (through torch's caching allocator) and reusable for repeated launches."""
+
+    def __init__(self, problems, ngroups=0, device=None):
+        import torch
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.problems = [tuple(p) + (None,) * (5 - len(p)) for p in problems]
+        self.ngroups = ngroups
+        self.caps = [capacity_bound(n, d, w) for n, d, o, w, _ in self.problems]
+        self.outs = [torch.empty(max(c, 1), dtype=torch.int32, device=dev) for c in self.caps]
+        self.stats = torch.zeros((len(self.problems), ctypes.sizeof(Stats)), dtype=torch.uint8,
+                                 device=dev)
+        self.jobs = (Job * len(self.problems))()
+        for k, (n, d, o, w, st) in enumerate(self.problems):
+            j = self.jobs[k]
+            j.prob = _problem(n, d, o, w)
+            j.strategy = _STRAT.get(st, st or 0)
+            j.d_out = self.outs[k].data_ptr()
+            j.capacity = self.caps[k]
+            j.d_stats = self.stats[k].data_ptr()
+        ws_bytes = batch_workspace_size(self.jobs, ngroups)
+        if ws_bytes == 0:
+            raise GcError(1, "gc_batch_workspace_size")
+        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+        base = (-ws.data_ptr()) % 256
+        self._ws_alloc = ws
+        self.workspace = ws[base:base + ws_bytes]
+
+    def launch(self, stream=None):
+        batch_generate_async(self.jobs, self.ngroups, self.workspace, stream=stream)
+
+    def results(self):
+        """[(code uint32 numpy array, Stats)] after the stream has finished."""
+        host_stats = self.stats.cpu().numpy()
+        out = []
+        for k in range(len(self.problems)):
+            s = Stats.from_buffer_copy(host_stats[k].tobytes())
+            code = self.outs[k][:min(s.codewords, self.caps[k])].cpu().numpy().view(np.uint32)
+            out.append((code, s))
+        return out
+
+
+def batch_workspace_size(jobs, ngroups=0) -> int:
+    return int(lib().gc_batch_workspace_size(jobs, len(jobs), ngroups))
+
+
+def batch_generate_async(jobs, ngroups, workspace, stream=None):
+    _check(lib().gc_batch_generate_async(jobs, len(jobs), ngroups, _ptr(workspace),
+                                         workspace.numel(), _stream(stream)),
+           "gc_batch_generate_async")
+
+
+def generate_batch(problems, ngroups=0, stream=None):
+    """Generate many codes in one launch; returns [(code, Stats)]."""
+    import torch
+    buf = BatchBuffers(problems, ngroups)
+    buf.launch(stream)
+    torch.cuda.synchronize()
+    return buf.results()
 
 
 def stats_from(t) -> Stats:

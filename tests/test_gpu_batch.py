@@ -1,0 +1,77 @@
+"""The batched sweep (gc_batch_generate_async): every job's code equals the
+oracle's, whatever the grouping of SMs and the mix of jobs around it."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_05398_gb300.workloads import batch_instances
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+BENCH = [(24, 8, "lex", -1), (20, 4, "lex", -1), (20, 4, "gray", -1), (20, 4, "grlex", -1),
+         (20, 4, "grevlex", -1)]
+
+
+def G():
+    import paper_1507_05398_gb300 as g
+    return g
+
+
+@pytest.mark.parametrize("ngroups", [5, 2, 1, 0])
+def test_bench_workload_as_one_batch(ngroups):
+    res = G().generate_batch(BENCH, ngroups=ngroups)
+    for (n, d, o, w), (code, st) in zip(BENCH, res):
+        assert st.status == 0
+        want, pos = oracle.greedy_ball(n, d, o, w, with_pos=True)
+        assert code.tolist() == want.tolist(), (n, d, o, ngroups)
+        assert st.dense_tests == oracle.dense_tests(pos, 1 << n)
+
+
+def test_mixed_small_batch_each_job_alone_and_in_the_mix():
+    """Jobs of very different sizes and strategies share one launch; each
+    result equals the oracle and the single-job launch."""
+    g = G()
+    probs = [(16, 3, "gray", -1, "bitmap"), (14, 5, "grevlex", 6, "distance"), (18, 4, "lex", -1, None),
+             (12, 3, "grlex", 4, "bitmap"), (17, 6, "gray", 7, None), (15, 2, "lex", -1, None),
+             (19, 7, "grlex", -1, "distance"), (10, 1, "gray", 4, None), (20, 5, "grevlex", -1, None)]
+    for ngroups in (0, 3, 1):
+        res = g.generate_batch(probs, ngroups=ngroups)
+        for (n, d, o, w, st_), (code, st) in zip(probs, res):
+            assert st.status == 0
+            want = oracle.greedy_ball(n, d, o, w)
+            assert code.tolist() == want.tolist(), (n, d, o, w, st_, ngroups)
+            alone = g.generate(n, d, o, w, strategy=st_).cpu().numpy().view(np.uint32)
+            assert alone.tolist() == want.tolist()
+
+
+def test_batch_sample_against_oracle():
+    """64 instances from the batched workload's generator (n <= 20 so the
+    oracle runs here), in one launch."""
+    probs = [p for p in batch_instances(512, 1507) if p[0] <= 20][:64]
+    res = G().generate_batch(probs)
+    for (n, d, o, w), (code, st) in zip(probs, res):
+        assert st.status == 0
+        assert code.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (n, d, o, w)
+
+
+def _batch_expected():
+    p = os.path.join(GOLDEN, "batch_expected.json")
+    return json.load(open(p))["codes"] if os.path.exists(p) else None
+
+
+@pytest.mark.skipif(_batch_expected() is None, reason="batch_expected.json not generated")
+def test_full_512_batch_against_stored_oracle():
+    """All 512 instances of the batched workload in one persistent launch,
+    compared with the oracle's stored digests."""
+    probs = batch_instances(512, 1507)
+    rows = _batch_expected()
+    res = G().generate_batch(probs)
+    for (n, d, o, w), row, (code, st) in zip(probs, rows, res):
+        assert (row["n"], row["d"], row["ordering"], row["weight"]) == (n, d, o, w)
+        assert st.status == 0
+        assert len(code) == row["size"]
+        assert hashlib.sha256(code.astype("<u4").tobytes()).hexdigest() == row["sha256"]
