@@ -109,8 +109,10 @@ typedef struct {
      * over windows, in [0] ball marking, [1] candidate generation and bitmap
      * lookup, [2] the newest-codeword test and compaction, [3] the split test
      * against older codewords, [4] publishing and waiting for the group,
-     * [5] gathering survivors, [6] resolving, [7] committing. */
-    uint64_t phase_cycles[8];
+     * [5] gathering survivors, [6] resolving, [7] committing; within [6]:
+     * [8] conflict matrix, [9] resolution rounds, [10] appending and the
+     * kill step; [11] counts resolution rounds (not cycles). */
+    uint64_t phase_cycles[12];
 } gc_stats;
 
 /* ---- information ------------------------------------------------------ */

@@ -18,8 +18,9 @@ constexpr int kResolveWords = kResolveBlock / 32;
 // Scratch the primitives below need, placed in shared memory by the caller.
 struct BlockScratch {
     uint32_t warp_sum[kWarps + 1];
-    uint32_t und[kResolveWords];
-    uint32_t accb[kResolveWords];
+    __align__(16) uint32_t und[kResolveWords];
+    __align__(16) uint32_t accb[kResolveWords];
+    uint32_t left[3];   // resolution rounds: "some entry still undecided"
     uint32_t flag_any;
 };
 
@@ -180,11 +181,23 @@ __device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, uint32_t* x, 
 //   acc/acc_off   receives accepted vectors/offsets in order (capacity >= n)
 //   Mt            kResolveWords x kResolveBlock words of shared memory
 // Returns the number accepted.
+// tim (optional, thread 0 only): cycles added to tim[0] matrix build,
+// tim[1] rounds, tim[2] append and kill step; tim[3] counts rounds.
 __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x, uint32_t* off,
                                                   uint8_t* dead, uint32_t n, int d,
                                                   uint32_t* acc, uint32_t* acc_off,
-                                                  uint32_t (*Mt)[kResolveBlock], uint64_t& nt) {
+                                                  uint32_t (*Mt)[kResolveBlock], uint64_t& nt,
+                                                  unsigned long long* tim = nullptr) {
     const int lane = lane_id(), warp = warp_id();
+    const bool timing = tim && threadIdx.x == 0;
+    long long t_last = timing ? clock64() : 0;
+    auto tick = [&](int k) {
+        if (timing) {
+            const long long t = clock64();
+            tim[k] += (unsigned long long)(t - t_last);
+            t_last = t;
+        }
+    };
     if (d <= 1) {  // nothing conflicts: every candidate is accepted
         for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
             acc[i] = x[i];
@@ -204,17 +217,29 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
         // shared-memory words across a warp: a warp owns a row, lane = column
         // within a 32-column word, and the word is the warp's ballot.  Words
         // right of the diagonal are never read, so they are not built.
-        for (uint32_t i = warp; i < P; i += kWarps) {
-            const uint32_t xi = bx[i];
-            const uint32_t last = i >> 5;  // word holding column i (partial)
-#pragma unroll 4
+        // four rows per warp share each column load
+        for (uint32_t i0 = warp * 4u; i0 < P; i0 += kWarps * 4u) {
+            const uint32_t nr = min(4u, P - i0);
+            const uint32_t x0 = bx[i0];
+            const uint32_t x1 = nr > 1 ? bx[i0 + 1] : 0u;
+            const uint32_t x2 = nr > 2 ? bx[i0 + 2] : 0u;
+            const uint32_t x3 = nr > 3 ? bx[i0 + 3] : 0u;
+            const uint32_t last = (i0 + nr - 1) >> 5;  // word holding the last row's diagonal
             for (uint32_t wd = 0; wd <= last; ++wd) {
                 const uint32_t j = (wd << 5) + lane;
-                const bool c = j < i && (__popc(xi ^ bx[j]) < d);
-                const unsigned bits = __ballot_sync(kFull, c);
-                if (lane == 0) Mt[wd][i] = bits;
+                const uint32_t c = bx[j < P ? j : 0];
+                const unsigned b0 = __ballot_sync(kFull, j < i0 && (__popc(x0 ^ c) < d));
+                const unsigned b1 = __ballot_sync(kFull, j < i0 + 1 && (__popc(x1 ^ c) < d));
+                const unsigned b2 = __ballot_sync(kFull, j < i0 + 2 && (__popc(x2 ^ c) < d));
+                const unsigned b3 = __ballot_sync(kFull, j < i0 + 3 && (__popc(x3 ^ c) < d));
+                if (lane == 0) {
+                    Mt[wd][i0] = b0;
+                    if (nr > 1) Mt[wd][i0 + 1] = b1;
+                    if (nr > 2) Mt[wd][i0 + 2] = b2;
+                    if (nr > 3) Mt[wd][i0 + 3] = b3;
+                }
             }
-            if (lane == 0) nt += i;
+            if (lane == 0) nt += 4u * i0 + 6u;
         }
         if (threadIdx.x < (unsigned)kResolveWords) {
             const uint32_t wb = threadIdx.x * 32u;
@@ -222,18 +247,34 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             bs.accb[threadIdx.x] = 0u;
         }
         __syncthreads();
-        for (;;) {
+        tick(0);
+        if (threadIdx.x < 3) bs.left[threadIdx.x] = 0u;
+        __syncthreads();
+        for (uint32_t round = 0;; ++round) {
+            if (timing) tim[3] += 1;
+            // slot of this round's flag; the next round's slot is cleared here:
+            // it was last read two rounds ago, and every thread has passed the
+            // previous round's first barrier since then
+            const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
+            if (threadIdx.x == 0) bs.left[next] = 0u;
             unsigned ba = 0, br = 0;
-            if ((uint32_t)warp < nwords) {
+            if ((uint32_t)warp < nwords && bs.und[warp] != 0u) {
                 const uint32_t i = warp * 32u + lane;
                 const bool u = (bs.und[warp] >> lane) & 1u;
                 bool a_now = false, r_now = false;
                 if (u) {
                     bool killed = false, blocked = false;
-                    for (uint32_t wd = 0; wd <= (uint32_t)warp; ++wd) {
-                        const uint32_t m = Mt[wd][i];
-                        killed |= (m & bs.accb[wd]) != 0u;
-                        blocked |= (m & bs.und[wd]) != 0u;
+                    const uint4* acc4 = reinterpret_cast<const uint4*>(bs.accb);
+                    const uint4* und4 = reinterpret_cast<const uint4*>(bs.und);
+                    for (uint32_t w4 = 0; w4 * 4u <= (uint32_t)warp; ++w4) {
+                        const uint4 av = acc4[w4], uv = und4[w4];
+                        const uint32_t wb = w4 * 4u;
+                        const uint32_t m0 = Mt[wb][i];
+                        const uint32_t m1 = wb + 1 <= (uint32_t)warp ? Mt[wb + 1][i] : 0u;
+                        const uint32_t m2 = wb + 2 <= (uint32_t)warp ? Mt[wb + 2][i] : 0u;
+                        const uint32_t m3 = wb + 3 <= (uint32_t)warp ? Mt[wb + 3][i] : 0u;
+                        killed |= ((m0 & av.x) | (m1 & av.y) | (m2 & av.z) | (m3 & av.w)) != 0u;
+                        blocked |= ((m0 & uv.x) | (m1 & uv.y) | (m2 & uv.z) | (m3 & uv.w)) != 0u;
                     }
                     r_now = killed;
                     a_now = !killed && !blocked;
@@ -244,13 +285,14 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             __syncthreads();
             if (lane == 0 && (uint32_t)warp < nwords) {
                 bs.accb[warp] |= ba;
-                bs.und[warp] &= ~(ba | br);
+                const uint32_t und = bs.und[warp] & ~(ba | br);
+                bs.und[warp] = und;
+                if (und) bs.left[slot] = 1u;
             }
             __syncthreads();
-            bool left = false;
-            for (uint32_t wd = 0; wd < nwords; ++wd) left |= bs.und[wd] != 0u;
-            if (!left) break;
+            if (bs.left[slot] == 0u) break;
         }
+        tick(1);
         // append the block's accepts in order
         const uint32_t nacc0 = nacc;
         for (uint32_t t0 = 0; t0 < P; t0 += kBlock) {
@@ -272,6 +314,7 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             end = start + P + kept;
         }
         start += P;
+        tick(2);
     }
     return nacc;
 }

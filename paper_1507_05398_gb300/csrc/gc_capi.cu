@@ -126,7 +126,7 @@ __global__ void all_accepted_stats(gc_stats* st, uint64_t N, int strategy) {
     st->survivors = 0;
     st->status = 0;
     st->strategy = strategy;
-    for (int k = 0; k < 8; ++k) st->phase_cycles[k] = 0;
+    for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
 }
 
 static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint32_t* d_out,

@@ -93,7 +93,7 @@ struct __align__(16) SweepSmem {
     uint8_t dead[kChunk];
     JobDesc job;
     GroupDesc grp;
-    unsigned long long phase[8];  // phase timers (thread 0 of the group's first CTA)
+    unsigned long long phase[12];  // phase timers (thread 0 of the group's first CTA)
     long long tprev;
     BlockScratch bs;
 };
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             gc_stats* st = a.jobs[a.job_order[jq]].stats;
             st->codewords = 0; st->candidates = 0; st->dense_tests = 0; st->executed_tests = 0;
             st->marks = 0; st->windows = 0; st->survivors = 0; st->status = 0; st->strategy = 0;
-            for (int k = 0; k < 8; ++k) st->phase_cycles[k] = 0;
+            for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
         }
 
     for (int jq = grp.job_begin; jq < grp.job_end && ok; ++jq) {
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
         uint64_t my_tests = 0, my_marks = 0, dense = 0, resolve_tests = 0;
         uint64_t windows = 0, surv_total = 0;
         if (timing)
-            for (int k = 0; k < 8; ++k) s.phase[k] = 0;
+            for (int k = 0; k < 12; ++k) s.phase[k] = 0;
         // adds the cycles since the last mark to phase k (first CTA, thread 0)
         auto mark_phase = [&](int k) {
             if (timing) {
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             // resolve in order; identical in every CTA of the group
             uint64_t rt = 0;
             const uint32_t nacc = block_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                                s.acc_off, s.M, rt);
+                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr);
             if (lb == 0) resolve_tests += rt;
             mark_phase(6);
 
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             job.stats->windows = windows;
             job.stats->survivors = surv_total;
             job.stats->strategy = job.strategy;
-            for (int k = 0; k < 8; ++k) job.stats->phase_cycles[k] = s.phase[k];
+            for (int k = 0; k < 12; ++k) job.stats->phase_cycles[k] = s.phase[k];
         }
         // the next job reuses the statistics-free scratch; make sure every CTA
         // of the group is done with this job's shared state first

@@ -65,9 +65,10 @@ class Stats(ctypes.Structure):
                 ("dense_tests", ctypes.c_uint64), ("executed_tests", ctypes.c_uint64),
                 ("marks", ctypes.c_uint64), ("windows", ctypes.c_uint64),
                 ("survivors", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("strategy", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 8)]
+                ("strategy", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 12)]
 
-    PHASES = ("mark", "generate", "test_new", "test_old", "wait", "gather", "resolve", "commit")
+    PHASES = ("mark", "generate", "test_new", "test_old", "wait", "gather", "resolve", "commit",
+              "res_matrix", "res_rounds", "res_append_kill", "rounds")
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_cycles"}
