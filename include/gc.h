@@ -196,6 +196,53 @@ int gc_batch_generate_async(const gc_job *jobs, int njobs, int ngroups,
                             void *workspace, size_t workspace_bytes,
                             void *stream);
 
+/* ---- serving: requests admitted while others run ------------------------ */
+
+/* Server settings (zero fields take the defaults in brackets). */
+typedef struct {
+    int max_n;              /* largest n accepted [28] */
+    int ngroups;            /* SM groups running requests concurrently
+                               [SMs / 8] */
+    size_t pool_bytes;      /* device pool for request outputs [4 GiB] */
+    int queue_capacity;     /* requests in flight at most [1024] */
+    uint64_t store_words;   /* per-group code store of the distance
+                               strategy [2^22 words] */
+    double idle_seconds;    /* the device loop leaves after this long
+                               without work and is restarted by the next
+                               submit [30] */
+} gc_server_config;
+
+typedef struct gc_server gc_server;
+
+/* Starts a server on the current device: allocates its pool and scratch and
+ * launches one persistent cooperative kernel (on its own stream) that keeps
+ * taking requests until gc_server_destroy.  While it runs it holds every SM;
+ * other work on the device waits for it. */
+int gc_server_create(const gc_server_config *cfg, gc_server **out);
+
+/* Admits one request (Section 3 problem) if a ring slot is free and its
+ * output -- gc_capacity_bound words -- fits in the pool (first fit);
+ * otherwise returns GC_ERR_CAPACITY and the caller retries after releasing
+ * finished requests.  strategy: gc_strategy.  Non-blocking. */
+int gc_server_submit(gc_server *s, const gc_problem *prob, int strategy,
+                     uint64_t *request_id);
+
+/* Reports up to max_ids requests that finished since the last poll. */
+int gc_server_poll(gc_server *s, uint64_t *done_ids, int max_ids, int *ndone);
+
+/* Copies a finished request's code (acceptance order) and statistics to
+ * host memory; *inout_count: capacity in, |C| out (GC_ERR_CAPACITY if it did
+ * not fit; the first capacity words are written).  host_out/host_stats may
+ * be NULL. */
+int gc_server_fetch(gc_server *s, uint64_t request_id, uint32_t *host_out,
+                    uint64_t *inout_count, gc_stats *host_stats);
+
+/* Returns a finished request's pool space and ring slot. */
+int gc_server_release(gc_server *s, uint64_t request_id);
+
+/* Stops the device loop (after the requests in flight), frees everything. */
+int gc_server_destroy(gc_server *s);
+
 /* Allocation-free form of gc_generate_async (the paper has no counterpart;
  * this is a service for callers).  Some callers cannot call cudaMalloc when
  * they need a code: code running while a CUDA stream is being captured,

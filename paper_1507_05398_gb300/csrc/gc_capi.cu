@@ -58,7 +58,7 @@ bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why
 // bitmap strategy cost ~ words OR-ed by ball marking (each an L2 atomic,
 // weighted as several tests) plus one lookup per candidate.  |C| is taken as
 // half the sphere-packing bound (lexicodes sit close to it).
-static void plan_for(const HostProblem& p, gc_plan_t* pl) {
+void plan_for(const HostProblem& p, gc_plan_t* pl) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/gc.h"
+#include "gc_device.cuh"
 
 namespace gc {
 
@@ -23,12 +24,54 @@ struct HostProblem {
 
 uint64_t binom64(int n, int k);
 bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why);
+// Strategy and launch shape for a problem (gc_plan).
+void plan_for(const HostProblem& p, gc_plan_t* pl);
 
 // Word-grouped ball: entries (e_high << 3) | radius for every high part of
 // weight <= d-1 over the n-5 word-index bits; radius = d-1-weight(e_high),
 // clipped to 7.  Its length:
 uint64_t high_ball_len(int n, int d);
 int launch_high_ball(int nh, int rad, uint32_t* d_out, uint32_t len, cudaStream_t s);
+
+// One code to generate, as the sweep kernel reads it (device memory for
+// batches, host-mapped memory for the server's ring).
+struct JobDesc {
+    Order ord;
+    int d;
+    int strategy;          // 1 distance, 2 bitmap
+    uint32_t* out;
+    uint64_t cap;
+    gc_stats* stats;
+    const uint32_t* hball;
+    uint32_t hball_len;
+    uint32_t wmin, wmax, target;
+};
+using JobDescHost = JobDesc;
+
+// Server: groups of equal size, scratch sized for the largest admissible
+// job, ball tables filled from the host on demand.
+struct ServeLayout {
+    int grid = 0, ngroups = 0, group_ctas = 0;
+    uint32_t cache_words = 0;
+    size_t smem_bytes = 0;
+    uint64_t store_words = 0;      // per group
+    uint64_t bitmap_bits = 0;      // per group
+    size_t off_err = 0, off_head = 0, off_groups = 0, off_hball = 0, hball_bytes = 0;
+    std::vector<size_t> g_flags, g_segx, g_segoff, g_store, g_bitmap;
+    size_t total = 0;
+    // ball tables already uploaded: key (n << 8 | d) -> (offset, length)
+    std::vector<std::pair<uint32_t, std::pair<size_t, uint32_t>>> hball_tables;
+    size_t hball_used = 0;
+    void* ws = nullptr;            // set once the workspace exists
+};
+
+bool serve_layout(const gc_server_config& cfg, ServeLayout* L, std::string* why);
+// Fills the descriptor of one request (uploads its ball table if needed).
+bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t* d_out,
+                    uint64_t cap, gc_stats* d_stats, JobDesc* desc, std::string* why);
+int launch_server(ServeLayout& L, void* ws, JobDesc* ring, unsigned* tail, unsigned* stop,
+                  unsigned long long* done, uint32_t capacity, double idle_seconds,
+                  cudaStream_t stream, std::string* why);
 
 // One job of a batch, checked and planned on the host.
 struct BatchJob {

@@ -44,19 +44,6 @@ constexpr int kMaxGroupCtas = 1024;
 constexpr int kMinGroup = 8;       // CTAs of the smallest group when sizes follow cost
 enum : int { kStratDistance = 1, kStratBitmap = 2 };
 
-// One code to generate (device-side descriptor).
-struct JobDesc {
-    Order ord;
-    int d;
-    int strategy;
-    uint32_t* out;
-    uint64_t cap;
-    gc_stats* stats;
-    const uint32_t* hball;
-    uint32_t hball_len;
-    uint32_t wmin, wmax, target;
-};
-
 // A group of CTAs and the scratch it owns.
 struct GroupDesc {
     int first_cta, ncta;
@@ -69,6 +56,20 @@ struct GroupDesc {
     uint32_t* bitmap;             // bitmap jobs: 2^n bits, vector-indexed
 };
 
+// Serving mode: jobs arrive while the kernel runs.  The host writes a job
+// descriptor into a ring in host-mapped memory, then raises `tail`; a group
+// claims the next published job with a compare-and-swap on `head`, runs it,
+// and raises done[slot] to (job index + 1).
+struct ServeQueue {
+    const JobDesc* descs;         // host-mapped ring [capacity]
+    const unsigned* tail;         // host-mapped: number of jobs published
+    const unsigned* stop;         // host-mapped: 1 = leave once idle
+    unsigned long long* done;     // host-mapped [capacity]
+    unsigned* head;               // device: number of jobs claimed
+    uint32_t capacity;
+    long long idle_cycles;        // bound on one wait for a new job
+};
+
 struct BatchArgs {
     const JobDesc* jobs;
     const int* job_order;
@@ -77,7 +78,35 @@ struct BatchArgs {
     unsigned* err;
     uint32_t cache_words;
     long long timeout_cycles;
+    ServeQueue queue;             // used when queue.descs != nullptr
 };
+
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Serving mode, thread 0 of a group's first CTA: claim the next published
+// job.  Returns its index + 1, or 0 when asked to stop (or idle too long).
+__device__ uint32_t serve_claim(const ServeQueue& q) {
+    const long long t0 = clock64();
+    for (;;) {
+        const unsigned t = ld_acquire_sys(q.tail);
+        unsigned h = ld_acquire_gpu(q.head);
+        while (h < t) {
+            const unsigned prev = atomicCAS(q.head, h, h + 1u);
+            if (prev == h) return h + 1u;
+            h = prev;
+        }
+        if (ld_acquire_sys(q.stop) != 0u) return 0u;
+        if (clock64() - t0 > q.idle_cycles) return 0u;
+        __nanosleep(256);
+    }
+}
 
 struct __align__(16) SweepSmem {
     uint32_t C[kMaxN + 1][kMaxN + 1];
@@ -214,9 +243,35 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
         }
 
-    for (int jq = grp.job_begin; jq < grp.job_end && ok; ++jq) {
-        if (tid == 0) s.job = a.jobs[a.job_order[jq]];
+    const bool serving = a.queue.descs != nullptr;
+    for (int jq = grp.job_begin; ok && (serving || jq < grp.job_end); ++jq) {
+        uint32_t serve_idx = 0;  // serving mode: job index + 1
+        if (serving) {
+            const uint32_t mine = (lb == 0 && tid == 0) ? serve_claim(a.queue) : 0u;
+            // every CTA of the group learns the claim (the sum of the counts)
+            serve_idx = group_exchange(s, grp.flags + (size_t)(seq & 1) * G, lb, G, seq, mine,
+                                       a.err, a.timeout_cycles + a.queue.idle_cycles, &ok);
+            ++seq;
+            if (!ok || serve_idx == 0) break;
+            if (tid == 0) {
+                // the descriptor was written before tail was raised (release),
+                // and serve_claim read tail with acquire; volatile loads keep
+                // stale cache lines of an earlier use of the slot out
+                const volatile uint32_t* src = reinterpret_cast<const volatile uint32_t*>(
+                    a.queue.descs + (serve_idx - 1) % a.queue.capacity);
+                uint32_t* dst = reinterpret_cast<uint32_t*>(&s.job);
+                for (uint32_t w = 0; w < sizeof(JobDesc) / 4; ++w) dst[w] = src[w];
+            }
+        } else if (tid == 0) {
+            s.job = a.jobs[a.job_order[jq]];
+        }
         __syncthreads();
+        if (serving && lb == 0 && tid == 0) {
+            gc_stats* st = s.job.stats;
+            st->codewords = 0; st->candidates = 0; st->dense_tests = 0; st->executed_tests = 0;
+            st->marks = 0; st->windows = 0; st->survivors = 0; st->status = 0; st->strategy = 0;
+            for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
+        }
         const JobDesc& job = s.job;
         const Order& o = job.ord;
         const int d = job.d;
@@ -466,8 +521,19 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
         // the next job reuses the statistics-free scratch; make sure every CTA
         // of the group is done with this job's shared state first
         __syncthreads();
+        if (serving && ok) {
+            // every CTA's statistics are in before the host is told
+            group_exchange(s, grp.flags + (size_t)(seq & 1) * G, lb, G, seq, 0, a.err,
+                           a.timeout_cycles, &ok);
+            ++seq;
+            if (lb == 0 && tid == 0) {
+                __threadfence_system();
+                st_release_sys_u64(a.queue.done + (serve_idx - 1) % a.queue.capacity,
+                                   (unsigned long long)serve_idx);
+            }
+        }
     }
-    if (tid == 0 && (!ok || ld_acquire_gpu(a.err) != 0u)) {
+    if (!serving && tid == 0 && (!ok || ld_acquire_gpu(a.err) != 0u)) {
         // report on every job this group owns (the failing one is among them)
         for (int jq = grp.job_begin; jq < grp.job_end; ++jq)
             atomicMax((int*)&a.jobs[a.job_order[jq]].stats->status, (int)GC_ERR_TIMEOUT);
@@ -776,6 +842,200 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
     e = cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(L.grid), dim3(kBlock), args,
                                     L.smem_bytes, stream);
     if (e != cudaSuccess) return cuda_fail("sweep launch");
+    return GC_OK;
+}
+
+}  // namespace gc
+
+namespace gc {
+
+// ------------------------------------------------------------------ server
+bool serve_layout(const gc_server_config& cfg, ServeLayout* L, std::string* why) {
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+        *why = "cannot query the CUDA device";
+        return false;
+    }
+    const size_t base = sizeof(SweepSmem);
+    if ((size_t)optin < base + 16) {
+        *why = "not enough shared memory per block";
+        return false;
+    }
+    int ng = cfg.ngroups > 0 ? cfg.ngroups : std::max(1, sms / 8);
+    ng = std::max(1, std::min(ng, sms));
+    L->ngroups = ng;
+    L->group_ctas = sms / ng;
+    L->grid = L->group_ctas * ng;
+    uint64_t room = (((size_t)optin - base) / 4) & ~(uint64_t)31;
+    L->cache_words = (uint32_t)std::min<uint64_t>(room, 16384);
+    L->smem_bytes = base + (size_t)L->cache_words * 4;
+    L->store_words = cfg.store_words;
+    L->bitmap_bits = 1ull << cfg.max_n;
+    size_t off = 0;
+    L->off_err = off;    off += align_up(256);
+    L->off_head = off;   off += align_up(256);
+    L->off_groups = off; off += align_up(sizeof(GroupDesc) * ng);
+    L->g_flags.assign(ng, 0); L->g_segx.assign(ng, 0); L->g_segoff.assign(ng, 0);
+    L->g_store.assign(ng, 0); L->g_bitmap.assign(ng, 0);
+    const int G = L->group_ctas;
+    for (int g = 0; g < ng; ++g) {
+        L->g_flags[g] = off;  off += align_up(sizeof(unsigned long long) * 2 * (G + 1));
+        L->g_segx[g] = off;   off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
+        L->g_segoff[g] = off; off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
+        L->g_store[g] = off;  off += align_up(sizeof(uint32_t) * L->store_words);
+        L->g_bitmap[g] = off; off += align_up((L->bitmap_bits + 31) / 32 * 4);
+    }
+    L->off_hball = off;
+    L->hball_bytes = 64ull << 20;
+    off += L->hball_bytes;
+    L->total = off;
+    return true;
+}
+
+// The word-grouped ball of radius d-1 (see high_ball_kernel), built on the
+// host so no kernel has to run beside the persistent one.
+static std::vector<uint32_t> host_high_ball(int n, int d) {
+    const int nh = n > 5 ? n - 5 : 0;
+    std::vector<uint32_t> out;
+    for (int k = 0; k <= d - 1 && k <= nh; ++k) {
+        const int r = std::min(d - 1 - k, 7);
+        if (k == 0) {
+            out.push_back((uint32_t)r);
+            continue;
+        }
+        // every nh-bit integer with k bits set, in increasing order
+        uint64_t y = (1ull << k) - 1;
+        while (y < (1ull << nh)) {
+            out.push_back(((uint32_t)y << 3) | (uint32_t)r);
+            const uint64_t low = y & (~y + 1);
+            const uint64_t up = y + low;
+            y = (((up ^ y) >> 2) / low) | up;
+        }
+    }
+    return out;
+}
+
+bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t* d_out,
+                    uint64_t cap, gc_stats* d_stats, JobDesc* D, std::string* why) {
+    gc_plan_t pl{};
+    plan_for(p, &pl);
+    if (strategy == GC_STRATEGY_DISTANCE || strategy == GC_STRATEGY_BITMAP) pl.strategy = strategy;
+    const bool dist_fits = p.bound <= (uint64_t)L.cache_words + L.store_words;
+    const bool bitmap_fits = (1ull << p.n) <= L.bitmap_bits && high_ball_len(p.n, p.d) < (1u << 24);
+    if (pl.strategy == GC_STRATEGY_DISTANCE && !dist_fits && bitmap_fits)
+        pl.strategy = GC_STRATEGY_BITMAP;
+    if (pl.strategy == GC_STRATEGY_BITMAP && !bitmap_fits && dist_fits)
+        pl.strategy = GC_STRATEGY_DISTANCE;
+    if ((pl.strategy == GC_STRATEGY_DISTANCE && !dist_fits) ||
+        (pl.strategy == GC_STRATEGY_BITMAP && !bitmap_fits)) {
+        *why = "request does not fit the server's scratch";
+        return false;
+    }
+    std::memset(D, 0, sizeof *D);
+    D->ord = make_order_host(p);
+    D->d = p.d;
+    D->strategy = pl.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
+    D->out = d_out;
+    D->cap = cap;
+    D->stats = d_stats;
+    D->target = 256;
+    D->wmax = (uint32_t)((uint64_t)L.group_ctas * kChunk);
+    D->wmin = std::min<uint32_t>(256, D->wmax);
+    if (D->strategy == kStratBitmap && p.d >= 1) {
+        const uint32_t key = ((uint32_t)p.n << 8) | (uint32_t)std::min(p.d, 255);
+        size_t at = 0;
+        uint32_t len = 0;
+        bool found = false;
+        for (auto& t : L.hball_tables)
+            if (t.first == key) { at = t.second.first; len = t.second.second; found = true; }
+        if (!found) {
+            std::vector<uint32_t> tab = host_high_ball(p.n, p.d);
+            const size_t bytes = align_up(tab.size() * 4);
+            if (L.hball_used + bytes > L.hball_bytes) {
+                *why = "ball-table arena full";
+                return false;
+            }
+            at = L.off_hball + L.hball_used;
+            len = (uint32_t)tab.size();
+            if (cudaMemcpy(static_cast<uint8_t*>(L.ws) + at, tab.data(), tab.size() * 4,
+                           cudaMemcpyHostToDevice) != cudaSuccess) {
+                *why = "ball-table upload";
+                return false;
+            }
+            L.hball_used += bytes;
+            L.hball_tables.push_back({key, {at, len}});
+        }
+        D->hball = reinterpret_cast<const uint32_t*>(static_cast<uint8_t*>(L.ws) + at);
+        D->hball_len = len;
+    }
+    return true;
+}
+
+int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail, unsigned* stop,
+                  unsigned long long* done, uint32_t capacity, double idle_seconds,
+                  cudaStream_t stream, std::string* why) {
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    L.ws = workspace;
+    std::vector<GroupDesc> gd(L.ngroups);
+    for (int g = 0; g < L.ngroups; ++g) {
+        GroupDesc& G = gd[g];
+        G.first_cta = g * L.group_ctas;
+        G.ncta = L.group_ctas;
+        G.job_begin = G.job_end = 0;
+        G.flags = reinterpret_cast<unsigned long long*>(ws + L.g_flags[g]);
+        G.seg_x = reinterpret_cast<uint32_t*>(ws + L.g_segx[g]);
+        G.seg_off = reinterpret_cast<uint32_t*>(ws + L.g_segoff[g]);
+        G.store = reinterpret_cast<uint32_t*>(ws + L.g_store[g]);
+        G.store_words = L.store_words;
+        G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
+    }
+    cudaError_t e;
+    auto cuda_fail = [&](const char* what) {
+        *why = std::string(what) + ": " + cudaGetErrorString(e);
+        return GC_ERR_CUDA;
+    };
+    if ((e = cudaMemcpyAsync(ws + L.off_groups, gd.data(), sizeof(GroupDesc) * L.ngroups,
+                             cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail("group descriptors");
+    if ((e = cudaMemsetAsync(ws + L.off_err, 0, 256, stream)) != cudaSuccess)
+        return cuda_fail("error word");
+    for (int g = 0; g < L.ngroups; ++g)
+        if ((e = cudaMemsetAsync(ws + L.g_flags[g], 0xff,
+                                 sizeof(unsigned long long) * 2 * (L.group_ctas + 1), stream)) !=
+            cudaSuccess)
+            return cuda_fail("group flags");
+    // the claim counter (zeroed when the server is created) is left as it
+    // is: a relaunch continues with the first published job no group has
+    // claimed
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail("server set-up");
+    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)L.smem_bytes)) != cudaSuccess)
+        return cuda_fail("shared memory attribute");
+    BatchArgs a{};
+    a.jobs = nullptr;
+    a.job_order = nullptr;
+    a.groups = reinterpret_cast<const GroupDesc*>(ws + L.off_groups);
+    a.ngroups = L.ngroups;
+    a.err = reinterpret_cast<unsigned*>(ws + L.off_err);
+    a.cache_words = L.cache_words;
+    a.timeout_cycles = 20000000000ll;
+    int dev = 0, clk_khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    a.queue.descs = ring;
+    a.queue.tail = tail;
+    a.queue.stop = stop;
+    a.queue.done = done;
+    a.queue.head = reinterpret_cast<unsigned*>(ws + L.off_head);
+    a.queue.capacity = capacity;
+    a.queue.idle_cycles = (long long)(idle_seconds * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(L.grid), dim3(kBlock), args,
+                                    L.smem_bytes, stream);
+    if (e != cudaSuccess) return cuda_fail("server launch");
     return GC_OK;
 }
 

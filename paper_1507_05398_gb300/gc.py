@@ -23,6 +23,7 @@ __all__ = [
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
     "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
     "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
+    "ServerConfig", "Server",
 ]
 
 LEX, GRAY, GRLEX, GREVLEX = 0, 1, 2, 3
@@ -100,6 +101,12 @@ _SIGS = {
     "gc_generate_noalloc": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan), _vp, _u64, _vp,
                                    _vp]),
     "gc_batch_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Job), _i32, _i32]),
+    "gc_server_create": (_i32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "gc_server_submit": (_i32, [_vp, ctypes.POINTER(Problem), _i32, ctypes.POINTER(_u64)]),
+    "gc_server_poll": (_i32, [_vp, ctypes.POINTER(_u64), _i32, ctypes.POINTER(_i32)]),
+    "gc_server_fetch": (_i32, [_vp, _u64, _vp, ctypes.POINTER(_u64), ctypes.c_void_p]),
+    "gc_server_release": (_i32, [_vp, _u64]),
+    "gc_server_destroy": (_i32, [_vp]),
     "gc_batch_generate_async": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp]),
     "gc_noalloc_scratch_bytes": (ctypes.c_size_t, []),
 }
@@ -411,3 +418,65 @@ def probe_test_rate() -> tuple[float, float]:
     r, c = ctypes.c_double(0), ctypes.c_double(0)
     _check(lib().gc_probe_test_rate(ctypes.byref(r), ctypes.byref(c)), "gc_probe_test_rate")
     return r.value, c.value
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_n", ctypes.c_int), ("ngroups", ctypes.c_int), ("pool_bytes", ctypes.c_size_t),
+                ("queue_capacity", ctypes.c_int), ("store_words", ctypes.c_uint64),
+                ("idle_seconds", ctypes.c_double)]
+
+
+class Server:
+    """Continuous-batching request server (gc_server_*): requests are admitted
+    by output footprint while others run in the same persistent launch."""
+
+    def __init__(self, max_n=28, ngroups=0, pool_bytes=0, queue_capacity=0, store_words=0,
+                 idle_seconds=0.0):
+        cfg = ServerConfig(max_n, ngroups, pool_bytes, queue_capacity, store_words, idle_seconds)
+        h = ctypes.c_void_p()
+        _check(lib().gc_server_create(ctypes.byref(cfg), ctypes.byref(h)), "gc_server_create")
+        self._h = h
+        self._ids = (_u64 * 4096)()
+
+    def submit(self, n, d, ordering="lex", weight=NO_WEIGHT, strategy=None):
+        """Request id, or None if not admitted now (pool or ring full)."""
+        rid = _u64(0)
+        rc = lib().gc_server_submit(self._h, ctypes.byref(_problem(n, d, ordering, weight)),
+                                    _STRAT.get(strategy, strategy or 0), ctypes.byref(rid))
+        if rc == 2:
+            return None
+        _check(rc, "gc_server_submit")
+        return int(rid.value)
+
+    def poll(self):
+        nd = _i32(0)
+        _check(lib().gc_server_poll(self._h, self._ids, len(self._ids), ctypes.byref(nd)),
+               "gc_server_poll")
+        return [int(self._ids[k]) for k in range(nd.value)]
+
+    def fetch(self, rid, capacity=None):
+        """(code as uint32 numpy array, Stats) of a finished request."""
+        st = Stats()
+        cnt = _u64(0)
+        rc = lib().gc_server_fetch(self._h, rid, None, ctypes.byref(cnt), ctypes.byref(st))
+        if rc not in (0, 2):
+            _check(rc, "gc_server_fetch")
+        buf = np.empty(max(int(cnt.value), 1), dtype=np.uint32)
+        cnt2 = _u64(len(buf))
+        _check(lib().gc_server_fetch(self._h, rid, buf.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(cnt2), ctypes.byref(st)), "gc_server_fetch")
+        return buf[:cnt2.value], st
+
+    def release(self, rid):
+        _check(lib().gc_server_release(self._h, rid), "gc_server_release")
+
+    def close(self):
+        if self._h:
+            _check(lib().gc_server_destroy(self._h), "gc_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
