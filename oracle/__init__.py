@@ -17,6 +17,10 @@ Parity status of each function (the pins are in ``tests/test_oracle.py``):
   greedy_ball (O2)           pinned (equal to O1 wherever O1 runs; Hamming
                              [31,26,3] closed form)
   verify (O3)                pinned (brute force: accepts exactly one subset)
+  greedy_selforth            pinned (Section 7: lex gives the extended Golay
+                             [24,12,8] and the baby Golay [22,11,6]; the
+                             codes are self-dual (Monroe's conjecture, checked
+                             where it is claimed); brute force for n <= 4)
   block_test / resolve /     pinned (brute force on small lists; resolve over the
   ball_mark / scan           whole order equals O1; the greedy code's balls
                              cover every candidate; scan of an empty map is the
@@ -67,7 +71,7 @@ def _load():
             lib.orc_order_list.argtypes = [i32, i32, i32, u32p, i64]
             lib.orc_order_sorted.restype = i64
             lib.orc_order_sorted.argtypes = [i32, i32, i32, u32p, i64]
-            for f in (lib.orc_greedy_pairwise, lib.orc_greedy_ball):
+            for f in (lib.orc_greedy_pairwise, lib.orc_greedy_ball, lib.orc_greedy_selforth):
                 f.restype = i64
                 f.argtypes = [i32, i32, i32, i32, u32p, i64p, i64]
             lib.orc_verify.restype = i32
@@ -140,6 +144,13 @@ def greedy_pairwise(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool 
 def greedy_ball(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool = False):
     """O2: the same greedy through radius-(d-1) exclusion balls over vectors."""
     return _greedy(_load().orc_greedy_ball, n, d, ordering, w, with_pos)
+
+
+def greedy_selforth(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool = False):
+    """Self-orthogonal greedy (Section 4.4): the pairwise greedy with the
+    extra constraint that every codeword is orthogonal to itself and to every
+    earlier codeword."""
+    return _greedy(_load().orc_greedy_selforth, n, d, ordering, w, with_pos)
 
 
 def verify(n: int, d: int, ordering, w: int, L) -> int:

@@ -406,3 +406,33 @@ int64_t orc_scan(int n, int ord, int w, const uint32_t *bitmap, uint64_t rank0,
     }
     return found;
 }
+
+/* ---- self-orthogonal greedy codes (Section 4.4) ------------------------- */
+/* The greedy of Section 3 with the extra constraint of Section 4.4: a vector
+ * is appended only if it is orthogonal to itself and to every codeword so
+ * far (over F_2, x.y = popcount(x AND y) mod 2), besides being at distance
+ * >= d from every codeword.  Pairwise form. */
+int64_t orc_greedy_selforth(int n, int d, int ord, int w, uint32_t *out, int64_t *pos,
+                            int64_t cap) {
+    if (!valid_args(n, ord, w) || d < 0) return ORC_EINVAL;
+    uint64_t ncand = orc_candidate_count(n, w);
+    uint64_t room = ncand < (1ull << 26) ? ncand : (1ull << 26);
+    uint32_t *C = (uint32_t *)malloc((room ? room : 1) * sizeof(uint32_t));
+    if (!C) return ORC_ENOMEM;
+    int64_t size = 0, idx = 0;
+    orc_iter it; iter_init(&it, n, ord, w);
+    uint32_t x;
+    while (iter_next(&it, &x)) {
+        int ok = (orc_popcount(x) % 2) == 0;          /* x.x = 0 */
+        for (int64_t j = 0; ok && j < size; ++j)
+            if (orc_distance(x, C[j]) < d || (orc_popcount(x & C[j]) % 2) != 0) ok = 0;
+        if (ok) {
+            if ((uint64_t)size >= room) { free(C); return ORC_ENOMEM; }
+            if (size < cap) { out[size] = x; if (pos) pos[size] = idx; }
+            C[size++] = x;
+        }
+        ++idx;
+    }
+    free(C);
+    return size;
+}

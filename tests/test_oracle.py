@@ -346,3 +346,52 @@ def test_step_scan(ordname):
         sub = oracle.order_list(n, ordname, w).tolist()
     assert oracle.scan(n, ordname, w, empty, 0, len(seq) if ordname == "gray" else comb(n, w)) \
         .tolist() == sub
+
+
+# ---------------------------------------------------------------- self-orthogonal
+def test_selforth_extended_and_baby_golay():
+    """Section 7: greedy self-orthogonal generation gives the extended Golay
+    code [24,12,8]; the baby Golay [22,11,6] (also named there) at n=22, d=6."""
+    rows = {(r[0], r[1]): r for r in _fixture_codes()}
+    C = oracle.greedy_selforth(24, 8, "lex")
+    assert len(C) == 4096 and weight_dist(C) == rows[(24, 8)][4]
+    B = oracle.greedy_selforth(22, 6, "lex")
+    assert len(B) == 2 ** 11
+    assert min(popc(x) for x in B[1:]) == 6
+    for code, n in ((C, 24), (B, 22)):  # self-dual: linear, self-orthogonal, 2^(n/2) words
+        assert xor_closed(code)
+        assert all(popc(int(a) & int(b)) % 2 == 0 for a in code[:40] for b in code)
+
+
+def test_selforth_extended_hamming_8():
+    C = oracle.greedy_selforth(8, 4, "lex")
+    assert len(C) == 16 and weight_dist(C) == {0: 1, 4: 14, 8: 1}
+
+
+def _selforth_characterised(n, d, seq):
+    found = []
+    N = len(seq)
+    for mask in range(1 << N):
+        members = [i for i in range(N) if mask >> i & 1]
+        if any(popc(seq[i]) % 2 for i in members):
+            continue
+        if any(popc(seq[i] ^ seq[j]) < d or popc(seq[i] & seq[j]) % 2
+               for i, j in itertools.combinations(members, 2)):
+            continue
+        ok = all(popc(seq[i]) % 2 or any(j < i and (popc(seq[i] ^ seq[j]) < d or
+                                                     popc(seq[i] & seq[j]) % 2)
+                                          for j in members)
+                 for i in range(N) if not mask >> i & 1)
+        if ok:
+            found.append([seq[i] for i in members])
+    return found
+
+
+@pytest.mark.parametrize("ordname", ORDERS)
+def test_selforth_bruteforce(ordname):
+    for n in (2, 3, 4):
+        seq = [int(x) for x in oracle.order_sorted(n, ordname)]
+        for d in range(0, n + 2):
+            found = _selforth_characterised(n, d, seq)
+            assert len(found) == 1
+            assert oracle.greedy_selforth(n, d, ordname).tolist() == found[0]
