@@ -155,6 +155,34 @@ def cpu_baseline_sample():
                       f"{secs:.1f} s)", "cpu": cpu_model()}
 
 
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1507_05398_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                   + glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the batched sweep from the committed ncu
+    summary, or None if the kernel sources changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "sweep_kernel_bench_workload_traffic.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in txt.splitlines()
+                if l.startswith(("traffic_bytes_per_launch:", "kernel_source_sha256_16:")))
+    if vals.get("kernel_source_sha256_16", "").strip() != kernel_source_hash():
+        return None
+    return int(vals["traffic_bytes_per_launch"].strip())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -286,7 +314,8 @@ def run_ours(args):
                 "ms_per_step": 1e3 * statistics.mean(e2e_times) if e2e_times else None},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "tests/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic() if not args.only else None,
                      "kernel": "gc::sweep_kernel",
                      "peak_source": "gc_probe_test_rate (register-operand XOR+popcount+compare, "
                                     "measured in this run)"},

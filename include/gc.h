@@ -76,12 +76,22 @@ typedef enum {
     GC_STRATEGY_BITMAP = 2    /* exclusion bitmap of radius-(d-1) balls */
 } gc_strategy;
 
+/* Extra constraints on the greedy. */
+enum {
+    GC_CONSTRAINT_NONE = 0,
+    /* Section 4.4: self-orthogonal greedy codes -- a candidate must also
+     * have even weight (be orthogonal to itself) and be orthogonal to every
+     * codeword so far (popcount(x AND c) even).  Distance strategy only. */
+    GC_CONSTRAINT_SELF_ORTHOGONAL = 1
+};
+
 /* One problem instance. */
 typedef struct {
     int n;              /* code length, 1..32 */
     int d;              /* minimum distance, >= 0 (d <= 1 accepts all) */
     int ordering;       /* gc_ordering */
     int weight;         /* GC_NO_WEIGHT or 0..n */
+    int constraint;     /* GC_CONSTRAINT_* (0 when the struct is zeroed) */
 } gc_problem;
 
 /* Launch plan chosen by gc_plan() (or given by the caller). */
@@ -98,7 +108,9 @@ typedef struct {
 typedef struct {
     uint64_t codewords;        /* |C| (the true size even past capacity) */
     uint64_t candidates;       /* candidates swept (rank-space size) */
-    uint64_t dense_tests;      /* sum over candidates of |C before it| */
+    uint64_t dense_tests;      /* sum over candidates of |C before it|
+                                  (0 when ranks are skipped: GRAY with a
+                                  weight, self-orthogonal problems) */
     uint64_t executed_tests;   /* distance tests the kernels executed */
     uint64_t marks;            /* bitmap words OR-ed by ball marking */
     uint64_t windows;          /* sequential window steps */
@@ -129,7 +141,10 @@ uint64_t gc_candidate_count(int n, int weight_or_none, int ordering);
 /* An upper bound on |C| that is always safe as an output capacity:
  * min(number of weight-admissible candidates, sphere-packing bound
  * floor(2^n / V(n, floor((d-1)/2)))) -- the radius-floor((d-1)/2) balls
- * around codewords are disjoint.  Returns 0 for invalid arguments. */
+ * around codewords are disjoint.  (A self-orthogonal code also has at most
+ * 2^floor(n/2) words: its span is a self-orthogonal linear code; the
+ * problem-struct entry points use that too.)  Returns 0 for invalid
+ * arguments. */
 uint64_t gc_capacity_bound(int n, int d, int weight_or_none);
 
 /* Choose a strategy and launch shape for a problem on the current device.

@@ -81,7 +81,7 @@ __device__ __forceinline__ uint32_t block_compact(BlockScratch& bs, uint32_t* x,
 // When shared_dead is given it is re-read every 32 codewords so that other
 // warps working on the same candidate can end this scan early.  Adds this
 // lane's tests to nt.
-template <bool kGlobalSrc>
+template <bool kGlobalSrc, bool kOrth = false>
 __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const uint32_t* src,
                                                uint32_t lo, uint32_t hi, int d,
                                                const volatile uint8_t* shared_dead, bool have,
@@ -98,8 +98,11 @@ __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const u
 #pragma unroll
             for (int q = 7; q >= 0; --q) {
                 const uint4 c = p4[q];
-                const bool hit = (__popc(x ^ c.w) < d) | (__popc(x ^ c.z) < d) |
-                                 (__popc(x ^ c.y) < d) | (__popc(x ^ c.x) < d);
+                bool hit = (__popc(x ^ c.w) < d) | (__popc(x ^ c.z) < d) |
+                           (__popc(x ^ c.y) < d) | (__popc(x ^ c.x) < d);
+                if (kOrth)  // Section 4.4: also a conflict if not orthogonal
+                    hit |= ((__popc(x & c.w) | __popc(x & c.z) | __popc(x & c.y) |
+                             __popc(x & c.x)) & 1u) != 0u;
                 is_dead |= hit;
             }
         } else {
@@ -109,6 +112,7 @@ __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const u
             for (uint32_t q = j; q > jlo; --q) {
                 const uint32_t c = kGlobalSrc ? ld_cg(src + q - 1) : src[q - 1];
                 is_dead |= (__popc(x ^ c) < d);
+                if (kOrth) is_dead |= (__popc(x & c) & 1) != 0;
             }
         }
         if (have) nt += j - jlo;
@@ -123,7 +127,7 @@ __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const u
 // the codeword range is split across warps as well (most recent slice to the
 // lowest warps), so a short list of hard candidates still keeps the whole CTA
 // busy.  Callers clear dead[] before and synchronise after.
-template <bool kGlobalSrc>
+template <bool kGlobalSrc, bool kOrth = false>
 __device__ __forceinline__ void block_test(const uint32_t* xs, uint32_t na, uint8_t* dead,
                                            const uint32_t* src, uint32_t lo, uint32_t hi, int d,
                                            uint64_t& nt) {
@@ -145,7 +149,7 @@ __device__ __forceinline__ void block_test(const uint32_t* xs, uint32_t na, uint
         const uint32_t top = (uint64_t)s * per >= len ? lo : hi - s * per;
         const uint32_t bot = (top - lo > per) ? top - per : lo;
         if (top <= bot) continue;
-        const bool now_dead = warp_scan_desc<kGlobalSrc>(
+        const bool now_dead = warp_scan_desc<kGlobalSrc, kOrth>(
             x, was_dead, src, bot, top, d,
             (have && splits > 1) ? (const volatile uint8_t*)(dead + i) : nullptr, have, nt);
         if (have && now_dead && !was_dead) dead[i] = 1;
@@ -187,7 +191,8 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
                                                   uint8_t* dead, uint32_t n, int d,
                                                   uint32_t* acc, uint32_t* acc_off,
                                                   uint32_t (*Mt)[kResolveBlock], uint64_t& nt,
-                                                  unsigned long long* tim = nullptr) {
+                                                  unsigned long long* tim = nullptr,
+                                                  bool orth = false) {
     const int lane = lane_id(), warp = warp_id();
     const bool timing = tim && threadIdx.x == 0;
     long long t_last = timing ? clock64() : 0;
@@ -198,7 +203,7 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             t_last = t;
         }
     };
-    if (d <= 1) {  // nothing conflicts: every candidate is accepted
+    if (d <= 1 && !orth) {  // nothing conflicts: every candidate is accepted
         for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
             acc[i] = x[i];
             if (acc_off) acc_off[i] = off[i];
@@ -228,10 +233,14 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             for (uint32_t wd = 0; wd <= last; ++wd) {
                 const uint32_t j = (wd << 5) + lane;
                 const uint32_t c = bx[j < P ? j : 0];
-                const unsigned b0 = __ballot_sync(kFull, j < i0 && (__popc(x0 ^ c) < d));
-                const unsigned b1 = __ballot_sync(kFull, j < i0 + 1 && (__popc(x1 ^ c) < d));
-                const unsigned b2 = __ballot_sync(kFull, j < i0 + 2 && (__popc(x2 ^ c) < d));
-                const unsigned b3 = __ballot_sync(kFull, j < i0 + 3 && (__popc(x3 ^ c) < d));
+                const unsigned b0 = __ballot_sync(
+                    kFull, j < i0 && ((__popc(x0 ^ c) < d) || (orth && (__popc(x0 & c) & 1))));
+                const unsigned b1 = __ballot_sync(
+                    kFull, j < i0 + 1 && ((__popc(x1 ^ c) < d) || (orth && (__popc(x1 & c) & 1))));
+                const unsigned b2 = __ballot_sync(
+                    kFull, j < i0 + 2 && ((__popc(x2 ^ c) < d) || (orth && (__popc(x2 & c) & 1))));
+                const unsigned b3 = __ballot_sync(
+                    kFull, j < i0 + 3 && ((__popc(x3 ^ c) < d) || (orth && (__popc(x3 & c) & 1))));
                 if (lane == 0) {
                     Mt[wd][i0] = b0;
                     if (nr > 1) Mt[wd][i0 + 1] = b1;
@@ -308,7 +317,10 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             uint32_t* ro = off ? off + start + P : nullptr;
             for (uint32_t i = threadIdx.x; i < rest; i += kBlock) dead[i] = 0;
             __syncthreads();
-            block_test<false>(rx, rest, dead, acc, nacc0, nacc, d, nt);
+            if (orth)
+                block_test<false, true>(rx, rest, dead, acc, nacc0, nacc, d, nt);
+            else
+                block_test<false, false>(rx, rest, dead, acc, nacc0, nacc, d, nt);
             __syncthreads();
             const uint32_t kept = block_compact(bs, rx, ro, dead, rest);
             end = start + P + kept;

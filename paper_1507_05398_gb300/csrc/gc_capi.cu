@@ -34,11 +34,16 @@ static uint64_t ball_volume(int n, int r) {
     return v;
 }
 
-bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why) {
+bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why, int constraint) {
     if (n < 1 || n > 32) { *why = "n must be in [1, 32]"; return false; }
     if (d < 0) { *why = "d must be >= 0"; return false; }
     if (ord < GC_ORDER_LEX || ord > GC_ORDER_GREVLEX) { *why = "unknown ordering"; return false; }
     if (w < -1 || w > n) { *why = "weight must be -1 or in [0, n]"; return false; }
+    if (constraint != GC_CONSTRAINT_NONE && constraint != GC_CONSTRAINT_SELF_ORTHOGONAL) {
+        *why = "unknown constraint";
+        return false;
+    }
+    p->orth = constraint == GC_CONSTRAINT_SELF_ORTHOGONAL;
     p->n = n;
     p->d = d;
     p->ord = ord;
@@ -51,6 +56,7 @@ bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why
     const uint64_t hb = (1ull << n) / ball_volume(n, t);
     p->bound = std::max<uint64_t>(1, std::min<uint64_t>(p->valid, hb));
     if (d <= 1) p->bound = p->valid;
+    if (p->orth) p->bound = std::min<uint64_t>(p->bound, 1ull << (n / 2));
     return true;
 }
 
@@ -67,7 +73,7 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
     pl->window_min = 256;
     pl->window_max = 0;
     pl->survivor_target = 256;
-    if (p.d <= 1) {
+    if (p.d <= 1 || p.orth) {  // orthogonality cannot be marked in a bitmap
         pl->strategy = GC_STRATEGY_DISTANCE;
         return;
     }
@@ -97,7 +103,7 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
 static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* out) {
     plan_for(p, out);
     if (in) {
-        if (in->strategy != GC_STRATEGY_AUTO) out->strategy = in->strategy;
+        if (in->strategy != GC_STRATEGY_AUTO && !p.orth) out->strategy = in->strategy;
         if (in->grid > 0) out->grid = in->grid;
         if (in->window_min) out->window_min = in->window_min;
         if (in->window_max) out->window_max = in->window_max;
@@ -132,7 +138,7 @@ __global__ void all_accepted_stats(gc_stats* st, uint64_t N, int strategy) {
 static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint32_t* d_out,
                                uint64_t capacity, gc_stats* d_stats, void* ws, size_t ws_bytes,
                                cudaStream_t s) {
-    if (p.d <= 1 && !p.filter) {
+    if (p.d <= 1 && !p.filter && !p.orth) {
         int rc = launch_unrank(p, 0, std::min(capacity, p.N), d_out, s);
         if (rc) return rc;
         all_accepted_stats<<<1, 1, 0, s>>>(d_stats, p.N, plan.strategy);
@@ -151,7 +157,7 @@ static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint
 }
 
 static size_t single_workspace(const HostProblem& p, const gc_plan_t& pl, std::string* why) {
-    if (p.d <= 1 && !p.filter) return 256;
+    if (p.d <= 1 && !p.filter && !p.orth) return 256;
     BatchJob job{p, pl, nullptr, 0, nullptr};
     BatchLayout L;
     if (!batch_layout(&job, 1, 1, &L, why)) return 0;
@@ -166,7 +172,8 @@ static int make_batch(const gc_job* jobs, int njobs, std::vector<BatchJob>* out)
         const gc_job& J = jobs[j];
         BatchJob B{};
         std::string why;
-        if (!make_problem(J.prob.n, J.prob.d, J.prob.ordering, J.prob.weight, &B.p, &why))
+        if (!make_problem(J.prob.n, J.prob.d, J.prob.ordering, J.prob.weight, &B.p, &why,
+                          J.prob.constraint))
             return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": " + why);
         gc_plan_t in{};
         in.strategy = J.strategy;
@@ -222,7 +229,7 @@ int gc_plan(const gc_problem* prob, gc_plan_t* out) {
     if (!prob || !out) return fail(GC_ERR_INVALID, "null argument");
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why))
+    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
         return fail(GC_ERR_INVALID, why);
     plan_for(p, out);
     return GC_OK;
@@ -232,7 +239,8 @@ size_t gc_workspace_size(const gc_problem* prob, const gc_plan_t* plan) {
     if (!prob) return 0;
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why)) return 0;
+    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
+        return 0;
     gc_plan_t pl;
     if (!resolve_plan(p, plan, &pl)) return 0;
     return single_workspace(p, pl, &why);
@@ -244,7 +252,7 @@ int gc_generate_async(const gc_problem* prob, const gc_plan_t* plan, uint32_t* d
     if (!prob || !d_stats || (!d_out && capacity > 0)) return fail(GC_ERR_INVALID, "null argument");
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why))
+    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
         return fail(GC_ERR_INVALID, why);
     gc_plan_t pl;
     if (!resolve_plan(p, plan, &pl)) return fail(GC_ERR_INVALID, "bad strategy");

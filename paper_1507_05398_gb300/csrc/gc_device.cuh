@@ -86,41 +86,45 @@ struct Order {
     int ord;
     int w;          // -1 = every weight
     bool filter;    // ranks whose vector has the wrong weight are skipped
+    bool even;      // only even-weight vectors are candidates (self-orthogonal)
     uint64_t N;     // rank-space size
     // graded orders without a weight: cum[k] = number of vectors of weight < k
     uint64_t cum[kMaxN + 2];
 };
 
-// Vector of rank r (r < N).  Returns false for a Gray rank of the wrong weight.
+// Vector of rank r (r < N).  Returns false when the rank is skipped: a Gray
+// rank of the wrong weight, or an odd-weight vector when only even ones are
+// candidates.
 __device__ __forceinline__ bool unrank(const Order& o, const uint32_t (*C)[kMaxN + 1], uint64_t r,
                                        uint32_t& x) {
     const int n = o.n;
+    bool ok = true;
     if (o.ord == kGray) {
         x = (uint32_t)(r ^ (r >> 1));
-        return !o.filter || __popc(x) == o.w;
-    }
-    if (o.ord == kLex && o.w < 0) {
+        ok = !o.filter || __popc(x) == o.w;
+    } else if (o.ord == kLex && o.w < 0) {
         x = (uint32_t)r;
-        return true;
-    }
-    int k;
-    uint32_t i;
-    if (o.w >= 0) {
-        k = o.w;
-        i = (uint32_t)r;
     } else {
-        // weight class of r: the last k with cum[k] <= r (classes ascend)
-        k = 0;
-        while (k < n && o.cum[k + 1] <= r) ++k;
-        i = (uint32_t)(r - o.cum[k]);
+        int k;
+        uint32_t i;
+        if (o.w >= 0) {
+            k = o.w;
+            i = (uint32_t)r;
+        } else {
+            // weight class of r: the last k with cum[k] <= r (classes ascend)
+            k = 0;
+            while (k < n && o.cum[k + 1] <= r) ++k;
+            i = (uint32_t)(r - o.cum[k]);
+        }
+        if (o.ord == kGrevlex) {
+            const uint32_t m = C[n][k] - 1 - i;
+            x = reverse_n(comb_unrank(C, n, k, m), n);
+        } else {
+            x = comb_unrank(C, n, k, i);  // kGrlex, or kLex restricted to weight w
+        }
     }
-    if (o.ord == kGrevlex) {
-        uint32_t m = C[n][k] - 1 - i;
-        x = reverse_n(comb_unrank(C, n, k, m), n);
-    } else {
-        x = comb_unrank(C, n, k, i);  // kGrlex, or kLex restricted to weight w
-    }
-    return true;
+    if (o.even && (__popc(x) & 1)) ok = false;
+    return ok;
 }
 
 // Rank of vector x in the full 2^n order (no weight).

@@ -16,6 +16,7 @@ namespace gc {
 // Fully checked problem description shared by the launchers.
 struct HostProblem {
     int n, d, ord, w;
+    bool orth;         // self-orthogonal constraint (Section 4.4)
     bool filter;       // GRAY with a weight: ranks of the wrong weight skipped
     uint64_t N;        // rank-space size
     uint64_t valid;    // number of candidates (C(n,w) or 2^n)
@@ -23,7 +24,8 @@ struct HostProblem {
 };
 
 uint64_t binom64(int n, int k);
-bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why);
+bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why,
+                  int constraint = GC_CONSTRAINT_NONE);
 // Strategy and launch shape for a problem (gc_plan).
 void plan_for(const HostProblem& p, gc_plan_t* pl);
 
@@ -45,6 +47,7 @@ struct JobDesc {
     const uint32_t* hball;
     uint32_t hball_len;
     uint32_t wmin, wmax, target;
+    int orth;              // self-orthogonal constraint
 };
 using JobDescHost = JobDesc;
 

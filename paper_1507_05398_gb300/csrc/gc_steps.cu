@@ -27,6 +27,7 @@ static Order make_order(const HostProblem& p, bool filter) {
     o.ord = p.ord;
     o.w = p.w;
     o.filter = filter;
+    o.even = false;
     o.N = p.N;
     uint64_t c = 0;
     for (int k = 0; k <= kMaxN + 1; ++k) {

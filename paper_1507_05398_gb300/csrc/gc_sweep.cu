@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             // strategy the older code (global store above the cache, then the
             // cache)
             mark_phase(1);
-            if (d >= 2 && na > 0) {
+            if ((d >= 2 || job.orth) && na > 0) {
                 // the committed code in newest-first order: prev (the previous
                 // window's accepts), then for the distance strategy the global
                 // store above the shared cache, then the cache.  It is scanned
@@ -400,20 +400,35 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     // prev: unified [0, nprev) -> prev[nprev-1 .. 0]
                     if (u < nprev) {
                         const uint32_t hi = min(u1, nprev);
-                        block_test<false>(s.list_x, na, s.dead, prev, nprev - hi, nprev - u, d, my_tests);
+                        if (job.orth)
+                            block_test<false, true>(s.list_x, na, s.dead, prev, nprev - hi,
+                                                    nprev - u, d, my_tests);
+                        else
+                            block_test<false, false>(s.list_x, na, s.dead, prev, nprev - hi,
+                                                     nprev - u, d, my_tests);
                     }
                     // global store: unified [nprev, nprev+nglob) -> store[Kprev-1 ..]
                     if (nglob && u1 > nprev && u < nprev + nglob) {
                         const uint32_t lo = max(u, nprev) - nprev, hi = min(u1, nprev + nglob) - nprev;
-                        block_test<true>(s.list_x, na, s.dead, grp.store, (uint32_t)Kprev - hi,
-                                         (uint32_t)Kprev - lo, d, my_tests);
+                        if (job.orth)
+                            block_test<true, true>(s.list_x, na, s.dead, grp.store,
+                                                   (uint32_t)Kprev - hi, (uint32_t)Kprev - lo, d,
+                                                   my_tests);
+                        else
+                            block_test<true, false>(s.list_x, na, s.dead, grp.store,
+                                                    (uint32_t)Kprev - hi, (uint32_t)Kprev - lo, d,
+                                                    my_tests);
                     }
                     // cache: unified [nprev+nglob, total) -> cache[ncached-1 .. 0]
                     if (ncached && u1 > nprev + nglob) {
                         const uint32_t base = nprev + nglob;
                         const uint32_t lo = max(u, base) - base, hi = u1 - base;
-                        block_test<false>(s.list_x, na, s.dead, cache, ncached - hi, ncached - lo, d,
-                                          my_tests);
+                        if (job.orth)
+                            block_test<false, true>(s.list_x, na, s.dead, cache, ncached - hi,
+                                                    ncached - lo, d, my_tests);
+                        else
+                            block_test<false, false>(s.list_x, na, s.dead, cache, ncached - hi,
+                                                     ncached - lo, d, my_tests);
                     }
                     __syncthreads();
                     na = block_compact(s.bs, s.list_x, s.list_off, s.dead, na);
@@ -461,7 +476,8 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             // resolve in order; identical in every CTA of the group
             uint64_t rt = 0;
             const uint32_t nacc = block_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr);
+                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
+                                                job.orth != 0);
             if (lb == 0) resolve_tests += rt;
             mark_phase(6);
 
@@ -470,7 +486,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 for (uint32_t i = tid; i < nacc; i += kBlock) {
                     const uint64_t pos = K + i;
                     if (pos < job.cap) job.out[pos] = cur[i];
-                    if (!o.filter) dense += o.N - 1 - (R0 + s.acc_off[i]);
+                    if (!o.filter && !o.even) dense += o.N - 1 - (R0 + s.acc_off[i]);
                 }
             }
             if (job.strategy == kStratDistance) {
@@ -588,6 +604,7 @@ static Order make_order_host(const HostProblem& p) {
     o.ord = p.ord;
     o.w = p.w;
     o.filter = p.filter;
+    o.even = p.orth;
     o.N = p.N;
     uint64_t c = 0;
     for (int k = 0; k <= kMaxN + 1; ++k) {
@@ -758,6 +775,7 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         D.ord = make_order_host(J.p);
         D.d = J.p.d;
         D.strategy = J.plan.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
+        D.orth = J.p.orth ? 1 : 0;
         D.out = J.d_out;
         D.cap = J.capacity;
         D.stats = J.d_stats;
@@ -938,6 +956,7 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
     D->ord = make_order_host(p);
     D->d = p.d;
     D->strategy = pl.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
+    D->orth = p.orth ? 1 : 0;
     D->out = d_out;
     D->cap = cap;
     D->stats = d_stats;

@@ -16,6 +16,7 @@ import numpy as np
 
 __all__ = [
     "LEX", "GRAY", "GRLEX", "GREVLEX", "NO_WEIGHT", "ORDERS",
+    "CONSTRAINT_NONE", "CONSTRAINT_SELF_ORTHOGONAL",
     "STRATEGY_AUTO", "STRATEGY_DISTANCE", "STRATEGY_BITMAP",
     "GcError", "Problem", "Plan", "Stats", "lib", "library_path", "header_functions",
     "strerror", "candidate_count", "capacity_bound", "plan", "workspace_size",
@@ -47,7 +48,15 @@ class GcError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("d", ctypes.c_int), ("ordering", ctypes.c_int),
-                ("weight", ctypes.c_int)]
+                ("weight", ctypes.c_int), ("constraint", ctypes.c_int)]
+
+
+CONSTRAINT_NONE, CONSTRAINT_SELF_ORTHOGONAL = 0, 1
+_CONSTRAINTS = {None: 0, "none": 0, "self_orthogonal": 1, "selforth": 1}
+
+
+def _constraint(c):
+    return _CONSTRAINTS[c] if (c is None or isinstance(c, str)) else int(c)
 
 
 class Plan(ctypes.Structure):
@@ -185,14 +194,21 @@ def capacity_bound(n: int, d: int, weight: int = NO_WEIGHT) -> int:
     return int(lib().gc_capacity_bound(n, d, weight))
 
 
-def _problem(n, d, ordering, weight):
-    return Problem(n, d, _ord(ordering), weight)
+def _bound(n, d, weight, constraint):
+    b = capacity_bound(n, d, weight)
+    if _constraint(constraint) == CONSTRAINT_SELF_ORTHOGONAL:
+        b = min(b, 1 << (n // 2))
+    return b
 
 
-def plan(n: int, d: int, ordering="lex", weight: int = NO_WEIGHT) -> Plan:
+def _problem(n, d, ordering, weight, constraint=None):
+    return Problem(n, d, _ord(ordering), weight, _constraint(constraint))
+
+
+def plan(n: int, d: int, ordering="lex", weight: int = NO_WEIGHT, constraint=None) -> Plan:
     p = Plan()
-    _check(lib().gc_plan(ctypes.byref(_problem(n, d, ordering, weight)), ctypes.byref(p)),
-           "gc_plan")
+    _check(lib().gc_plan(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
+                         ctypes.byref(p)), "gc_plan")
     return p
 
 
@@ -207,20 +223,21 @@ def _plan_arg(strategy=None, **kw):
     return p
 
 
-def workspace_size(n, d, ordering="lex", weight=NO_WEIGHT, strategy=None, **plan_kw) -> int:
+def workspace_size(n, d, ordering="lex", weight=NO_WEIGHT, strategy=None, constraint=None,
+                   **plan_kw) -> int:
     pl = _plan_arg(strategy, **plan_kw)
-    return int(lib().gc_workspace_size(ctypes.byref(_problem(n, d, ordering, weight)),
+    return int(lib().gc_workspace_size(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
                                        ctypes.byref(pl) if pl is not None else None))
 
 
 # ---------------------------------------------------------------- the sweep
 def generate_async(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, workspace,
-                   strategy=None, stream=None, **plan_kw):
+                   strategy=None, stream=None, constraint=None, **plan_kw):
     """gc_generate_async: out (uint32 CUDA tensor, its length is the capacity),
     stats (uint8 CUDA tensor of sizeof(gc_stats) bytes), workspace (uint8 CUDA
     tensor of >= workspace_size bytes, 256-byte aligned)."""
     pl = _plan_arg(strategy, **plan_kw)
-    rc = lib().gc_generate_async(ctypes.byref(_problem(n, d, ordering, weight)),
+    rc = lib().gc_generate_async(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
                                  ctypes.byref(pl) if pl is not None else None,
                                  _ptr(out), out.numel() if out is not None else 0, _ptr(stats),
                                  _ptr(workspace), workspace.numel(), _stream(stream))
@@ -228,12 +245,12 @@ def generate_async(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, worksp
 
 
 def generate_noalloc(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, strategy=None,
-                     stream=None, **plan_kw):
+                     stream=None, constraint=None, **plan_kw):
     """gc_generate_noalloc: like generate_async but the library allocates
     nothing -- its scratch is a static device array (see include/gc.h).  For
     callers that cannot allocate device memory when they need a code."""
     pl = _plan_arg(strategy, **plan_kw)
-    rc = lib().gc_generate_noalloc(ctypes.byref(_problem(n, d, ordering, weight)),
+    rc = lib().gc_generate_noalloc(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
                                    ctypes.byref(pl) if pl is not None else None,
                                    _ptr(out), out.numel() if out is not None else 0, _ptr(stats),
                                    _stream(stream))
@@ -256,16 +273,16 @@ class BatchBuffers:
     def __init__(self, problems, ngroups=0, device=None):
         import torch
         dev = device or torch.device("cuda", torch.cuda.current_device())
-        self.problems = [tuple(p) + (None,) * (5 - len(p)) for p in problems]
+        self.problems = [tuple(p) + (None,) * (6 - len(p)) for p in problems]
         self.ngroups = ngroups
-        self.caps = [capacity_bound(n, d, w) for n, d, o, w, _ in self.problems]
+        self.caps = [_bound(n, d, w, c) for n, d, o, w, _, c in self.problems]
         self.outs = [torch.empty(max(c, 1), dtype=torch.int32, device=dev) for c in self.caps]
         self.stats = torch.zeros((len(self.problems), ctypes.sizeof(Stats)), dtype=torch.uint8,
                                  device=dev)
         self.jobs = (Job * len(self.problems))()
-        for k, (n, d, o, w, st) in enumerate(self.problems):
+        for k, (n, d, o, w, st, c) in enumerate(self.problems):
             j = self.jobs[k]
-            j.prob = _problem(n, d, o, w)
+            j.prob = _problem(n, d, o, w, c)
             j.strategy = _STRAT.get(st, st or 0)
             j.d_out = self.outs[k].data_ptr()
             j.capacity = self.caps[k]
@@ -318,13 +335,13 @@ def stats_from(t) -> Stats:
 
 
 def generate(n, d, ordering="lex", weight=NO_WEIGHT, *, strategy=None, stream=None,
-             capacity=None, return_stats=False, **plan_kw):
+             capacity=None, return_stats=False, constraint=None, **plan_kw):
     """Whole sweep on the current CUDA device; returns a uint32 CUDA tensor
     with the code in acceptance order (and the Stats if asked)."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
-    cap = capacity_bound(n, d, weight) if capacity is None else capacity
-    ws_bytes = workspace_size(n, d, ordering, weight, strategy, **plan_kw)
+    cap = _bound(n, d, weight, constraint) if capacity is None else capacity
+    ws_bytes = workspace_size(n, d, ordering, weight, strategy, constraint, **plan_kw)
     if ws_bytes == 0:
         raise GcError(1, "gc_workspace_size")
     out = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
@@ -333,7 +350,8 @@ def generate(n, d, ordering="lex", weight=NO_WEIGHT, *, strategy=None, stream=No
     base = (-ws.data_ptr()) % 256
     ws_al = ws[base:base + ws_bytes]
     generate_async(n, d, ordering, weight, out=out[:cap] if cap else None, stats=st,
-                   workspace=ws_al, strategy=strategy, stream=stream, **plan_kw)
+                   workspace=ws_al, strategy=strategy, stream=stream, constraint=constraint,
+                   **plan_kw)
     s = stats_from(st)
     if s.status != 0:
         raise GcError(int(s.status), "sweep")
@@ -438,10 +456,11 @@ class Server:
         self._h = h
         self._ids = (_u64 * 4096)()
 
-    def submit(self, n, d, ordering="lex", weight=NO_WEIGHT, strategy=None):
+    def submit(self, n, d, ordering="lex", weight=NO_WEIGHT, strategy=None, constraint=None):
         """Request id, or None if not admitted now (pool or ring full)."""
         rid = _u64(0)
-        rc = lib().gc_server_submit(self._h, ctypes.byref(_problem(n, d, ordering, weight)),
+        rc = lib().gc_server_submit(self._h, ctypes.byref(_problem(n, d, ordering, weight,
+                                                                   constraint)),
                                     _STRAT.get(strategy, strategy or 0), ctypes.byref(rid))
         if rc == 2:
             return None
