@@ -21,6 +21,9 @@ Parity status of each function (the pins are in ``tests/test_oracle.py``):
                              [24,12,8] and the baby Golay [22,11,6]; the
                              codes are self-dual (Monroe's conjecture, checked
                              where it is claimed); brute force for n <= 4)
+  greedy_border              pinned (the standard basis gives lex, the Gray basis
+                             gives Gray; B-greedy codes are linear; brute force
+                             over all subsets for n <= 4)
   block_test / resolve /     pinned (brute force on small lists; resolve over the
   ball_mark / scan           whole order equals O1; the greedy code's balls
                              cover every candidate; scan of an empty map is the
@@ -74,6 +77,10 @@ def _load():
             for f in (lib.orc_greedy_pairwise, lib.orc_greedy_ball, lib.orc_greedy_selforth):
                 f.restype = i64
                 f.argtypes = [i32, i32, i32, i32, u32p, i64p, i64]
+            lib.orc_greedy_border.restype = i64
+            lib.orc_greedy_border.argtypes = [i32, i32, u32p, i32, u32p, i64p, i64]
+            lib.orc_border_vector.restype = ctypes.c_uint32
+            lib.orc_border_vector.argtypes = [i32, u32p, ctypes.c_uint64]
             lib.orc_verify.restype = i32
             lib.orc_verify.argtypes = [i32, i32, i32, i32, u32p, i64]
             lib.orc_distance.restype = i32
@@ -151,6 +158,27 @@ def greedy_selforth(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool 
     extra constraint that every codeword is orthogonal to itself and to every
     earlier codeword."""
     return _greedy(_load().orc_greedy_selforth, n, d, ordering, w, with_pos)
+
+
+def greedy_border(n: int, d: int, basis, w: int = -1, with_pos: bool = False):
+    """Greedy over the B-ordering of an ordered basis (Section 4.3): rank r is
+    the XOR of basis[j] over the set bits j of r."""
+    b = np.ascontiguousarray(np.asarray(basis, dtype=np.uint32))
+    if len(b) != n:
+        raise ValueError("basis must have n vectors")
+    cap = min((1 << n) if w < 0 else candidate_count(n, w), 1 << 26)
+    out = np.empty(max(cap, 1), dtype=np.uint32)
+    pos = np.empty(max(cap, 1), dtype=np.int64) if with_pos else None
+    k = _load().orc_greedy_border(n, d, _ptr(b), w, _ptr(out), _ptr(pos) if with_pos else None,
+                                  cap)
+    if k < 0:
+        raise RuntimeError(f"oracle error {k} (basis dependent or bad arguments)")
+    return (out[:k].copy(), pos[:k].copy()) if with_pos else out[:k].copy()
+
+
+def border_vector(n: int, basis, r: int) -> int:
+    b = np.ascontiguousarray(np.asarray(basis, dtype=np.uint32))
+    return int(_load().orc_border_vector(n, _ptr(b), r))
 
 
 def verify(n: int, d: int, ordering, w: int, L) -> int:

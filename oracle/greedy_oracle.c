@@ -436,3 +436,61 @@ int64_t orc_greedy_selforth(int n, int d, int ord, int w, uint32_t *out, int64_t
     free(C);
     return size;
 }
+
+/* ---- B-orderings (Section 4.3) ------------------------------------------ */
+/* For an ordered basis B = {b_1, ..., b_n} of F_2^n the B-ordering lists
+ * 0, b_1, b_2, b_2+b_1, b_3, b_3+b_1, ...: rank r is the sum (XOR) of the b_j
+ * whose index j-1 is a set bit of r.  basis[j-1] holds b_j.  Returns 1 iff
+ * the n vectors are linearly independent over F_2 (plain elimination). */
+static int basis_independent(int n, const uint32_t *basis) {
+    uint32_t rows[32];
+    for (int j = 0; j < n; ++j) rows[j] = basis[j] & (uint32_t)((n == 32) ? 0xffffffffu : ((1u << n) - 1u));
+    for (int j = 0; j < n; ++j) if (rows[j] != basis[j]) return 0;
+    int rank = 0;
+    for (int bit = n - 1; bit >= 0; --bit) {
+        int piv = -1;
+        for (int j = rank; j < n; ++j)
+            if (rows[j] >> bit & 1u) { piv = j; break; }
+        if (piv < 0) continue;
+        uint32_t t = rows[piv]; rows[piv] = rows[rank]; rows[rank] = t;
+        for (int j = 0; j < n; ++j)
+            if (j != rank && (rows[j] >> bit & 1u)) rows[j] ^= rows[rank];
+        ++rank;
+    }
+    return rank == n;
+}
+
+uint32_t orc_border_vector(int n, const uint32_t *basis, uint64_t r) {
+    uint32_t v = 0;
+    for (int j = 0; j < n; ++j)
+        if (r >> j & 1u) v ^= basis[j];
+    return v;
+}
+
+/* The greedy of Section 3 over a B-ordering (optionally only weight-w
+ * vectors, skipped in place like GRAY), pairwise form. */
+int64_t orc_greedy_border(int n, int d, const uint32_t *basis, int w, uint32_t *out,
+                          int64_t *pos, int64_t cap) {
+    if (n < 1 || n > 32 || d < 0 || w < -1 || w > n || !basis_independent(n, basis))
+        return ORC_EINVAL;
+    uint64_t room = (w < 0 ? (1ull << n) : binom(n, w));
+    if (room > (1ull << 26)) room = 1ull << 26;
+    uint32_t *C = (uint32_t *)malloc((room ? room : 1) * sizeof(uint32_t));
+    if (!C) return ORC_ENOMEM;
+    int64_t size = 0, idx = 0;
+    for (uint64_t r = 0; r < (1ull << n); ++r) {
+        const uint32_t x = orc_border_vector(n, basis, r);
+        if (w >= 0 && orc_popcount(x) != w) continue;
+        int ok = 1;
+        for (int64_t j = 0; j < size; ++j)
+            if (orc_distance(x, C[j]) < d) { ok = 0; break; }
+        if (ok) {
+            if ((uint64_t)size >= room) { free(C); return ORC_ENOMEM; }
+            if (size < cap) { out[size] = x; if (pos) pos[size] = idx; }
+            C[size++] = x;
+        }
+        ++idx;
+    }
+    free(C);
+    return size;
+}

@@ -395,3 +395,62 @@ def test_selforth_bruteforce(ordname):
             found = _selforth_characterised(n, d, seq)
             assert len(found) == 1
             assert oracle.greedy_selforth(n, d, ordname).tolist() == found[0]
+
+
+# ---------------------------------------------------------------- B-orderings
+def random_basis(n, rng):
+    """An invertible n x n matrix over F_2 (rows = basis vectors), drawn by
+    rejection."""
+    while True:
+        rows = [int(v) for v in rng.integers(0, 1 << n, n, dtype=np.uint64)]
+        m, rank = list(rows), 0
+        for bit in range(n - 1, -1, -1):
+            piv = next((j for j in range(rank, n) if m[j] >> bit & 1), None)
+            if piv is None:
+                continue
+            m[rank], m[piv] = m[piv], m[rank]
+            for j in range(n):
+                if j != rank and m[j] >> bit & 1:
+                    m[j] ^= m[rank]
+            rank += 1
+        if rank == n:
+            return rows
+
+
+def test_border_sequence_definition():
+    """Section 4.3: {0, b1, b2, b2+b1, b3, b3+b1, b3+b2, b3+b2+b1, b4, ...}."""
+    b = [0b0011, 0b0101, 0b1110, 0b0001]
+    seq = [oracle.border_vector(4, b, r) for r in range(16)]
+    assert seq[:9] == [0, b[0], b[1], b[1] ^ b[0], b[2], b[2] ^ b[0], b[2] ^ b[1],
+                       b[2] ^ b[1] ^ b[0], b[3]]
+    assert sorted(seq) == list(range(16))
+
+
+@pytest.mark.parametrize("n,d", [(8, 3), (10, 4), (12, 5), (13, 3)])
+def test_border_standard_and_gray_bases(n, d):
+    std = [1 << j for j in range(n)]
+    gray = [(1 << j) ^ (1 << (j - 1)) if j else 1 for j in range(n)]
+    assert oracle.greedy_border(n, d, std).tolist() == oracle.greedy_pairwise(n, d, "lex").tolist()
+    assert oracle.greedy_border(n, d, gray).tolist() == oracle.greedy_pairwise(n, d, "gray").tolist()
+
+
+@pytest.mark.parametrize("n,d", [(9, 3), (11, 4), (12, 6)])
+def test_border_codes_are_linear(n, d):
+    rng = np.random.default_rng(n * 10 + d)
+    for _ in range(3):
+        C = oracle.greedy_border(n, d, random_basis(n, rng))
+        assert len(C) & (len(C) - 1) == 0
+        assert xor_closed(C)
+
+
+def test_border_bruteforce_and_dependent_basis():
+    rng = np.random.default_rng(3)
+    for n in (2, 3, 4):
+        b = random_basis(n, rng)
+        seq = [oracle.border_vector(n, b, r) for r in range(1 << n)]
+        for d in range(0, n + 2):
+            found = greedy_characterised(n, d, seq)
+            assert len(found) == 1
+            assert oracle.greedy_border(n, d, b).tolist() == found[0]
+    with pytest.raises(RuntimeError):
+        oracle.greedy_border(4, 2, [1, 2, 3, 8])
