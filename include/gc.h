@@ -22,7 +22,7 @@
  *  - Constant weight: weight_or_none in [0, n] keeps only weight-w vectors, in
  *    the same relative order; GC_NO_WEIGHT (-1) keeps all 2^n vectors.
  *  - "Rank space" of a problem: 2^n ranks when no weight is given or the
- *    order is GRAY (Gray ranks of the wrong weight are skipped); C(n, w)
+ *    order is GRAY or BASIS (ranks of the wrong weight are skipped); C(n, w)
  *    ranks for LEX, GRLEX and GREVLEX with a weight (LEX and GRLEX restricted
  *    to one weight are the same sequence).
  *  - Return value: GC_OK (0) or a positive GC_ERR_* code; no exception or
@@ -52,7 +52,11 @@ typedef enum {
     GC_ORDER_LEX = 0,
     GC_ORDER_GRAY = 1,
     GC_ORDER_GRLEX = 2,
-    GC_ORDER_GREVLEX = 3
+    GC_ORDER_GREVLEX = 3,
+    /* Section 4.3: the B-ordering of an ordered basis b_1..b_n of F_2^n --
+     * rank r is the XOR of the b_j over the set bits j-1 of r (0, b_1, b_2,
+     * b_2+b_1, b_3, ...).  Needs gc_problem.basis; rank space as for GRAY. */
+    GC_ORDER_BASIS = 4
 } gc_ordering;
 
 #define GC_NO_WEIGHT (-1)
@@ -92,6 +96,9 @@ typedef struct {
     int ordering;       /* gc_ordering */
     int weight;         /* GC_NO_WEIGHT or 0..n */
     int constraint;     /* GC_CONSTRAINT_* (0 when the struct is zeroed) */
+    const uint32_t *basis; /* GC_ORDER_BASIS: host array of n linearly
+                              independent vectors, basis[j-1] = b_j (read
+                              during the call); NULL otherwise */
 } gc_problem;
 
 /* Launch plan chosen by gc_plan() (or given by the caller). */

@@ -187,12 +187,13 @@ __device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, uint32_t* x, 
 // Returns the number accepted.
 // tim (optional, thread 0 only): cycles added to tim[0] matrix build,
 // tim[1] rounds, tim[2] append and kill step; tim[3] counts rounds.
+template <bool kOrth = false>
 __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x, uint32_t* off,
                                                   uint8_t* dead, uint32_t n, int d,
                                                   uint32_t* acc, uint32_t* acc_off,
                                                   uint32_t (*Mt)[kResolveBlock], uint64_t& nt,
-                                                  unsigned long long* tim = nullptr,
-                                                  bool orth = false) {
+                                                  unsigned long long* tim = nullptr) {
+    constexpr bool orth = kOrth;
     const int lane = lane_id(), warp = warp_id();
     const bool timing = tim && threadIdx.x == 0;
     long long t_last = timing ? clock64() : 0;
@@ -317,10 +318,7 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
             uint32_t* ro = off ? off + start + P : nullptr;
             for (uint32_t i = threadIdx.x; i < rest; i += kBlock) dead[i] = 0;
             __syncthreads();
-            if (orth)
-                block_test<false, true>(rx, rest, dead, acc, nacc0, nacc, d, nt);
-            else
-                block_test<false, false>(rx, rest, dead, acc, nacc0, nacc, d, nt);
+            block_test<false, kOrth>(rx, rest, dead, acc, nacc0, nacc, d, nt);
             __syncthreads();
             const uint32_t kept = block_compact(bs, rx, ro, dead, rest);
             end = start + P + kept;

@@ -34,10 +34,76 @@ static uint64_t ball_volume(int n, int r) {
     return v;
 }
 
-bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why, int constraint) {
+// Inverts the basis over F_2 (Gauss-Jordan on [B | I], B's columns = basis
+// vectors): inv[j] = row j of B^-1.  False if the vectors are dependent.
+static bool invert_basis(int n, const uint32_t* basis, uint32_t* inv) {
+    const uint32_t mask = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+    // rows of B: row i = bit i of every basis vector; augment with identity
+    uint32_t row[32], aug[32];
+    for (int i = 0; i < n; ++i) {
+        row[i] = 0;
+        for (int j = 0; j < n; ++j) row[i] |= ((basis[j] >> i) & 1u) << j;
+        aug[i] = 1u << i;
+    }
+    for (int j = 0; j < n; ++j)
+        if ((basis[j] & ~mask) != 0u) return false;
+    for (int col = 0; col < n; ++col) {
+        int piv = -1;
+        for (int i = col; i < n; ++i)
+            if ((row[i] >> col) & 1u) { piv = i; break; }
+        if (piv < 0) return false;
+        std::swap(row[piv], row[col]);
+        std::swap(aug[piv], aug[col]);
+        for (int i = 0; i < n; ++i)
+            if (i != col && ((row[i] >> col) & 1u)) {
+                row[i] ^= row[col];
+                aug[i] ^= aug[col];
+            }
+    }
+    // now B^-1 = aug as a matrix whose row i is aug[i] read by columns:
+    // (B^-1)[i][k] = bit k of aug[i]; rank bit i of v = parity(aug[i] & v)
+    for (int i = 0; i < n; ++i) inv[i] = aug[i];
+    return true;
+}
+
+bool make_problem(const gc_problem& q, HostProblem* p, std::string* why) {
+    return make_problem(q.n, q.d, q.ordering, q.weight, p, why, q.constraint, q.basis);
+}
+
+Order order_of(const HostProblem& p, bool filter, bool even) {
+    Order o{};
+    o.n = p.n;
+    o.ord = p.ord;
+    o.w = p.w;
+    o.filter = filter;
+    o.even = even;
+    o.N = p.N;
+    uint64_t c = 0;
+    for (int k = 0; k <= kMaxN + 1; ++k) {
+        o.cum[k] = c;
+        if (k <= p.n) c += binom64(p.n, k);
+    }
+    for (int j = 0; j < 32; ++j) {
+        o.basis[j] = p.basis[j];
+        o.inv[j] = p.inv[j];
+    }
+    return o;
+}
+
+bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why, int constraint,
+                  const uint32_t* basis) {
     if (n < 1 || n > 32) { *why = "n must be in [1, 32]"; return false; }
     if (d < 0) { *why = "d must be >= 0"; return false; }
-    if (ord < GC_ORDER_LEX || ord > GC_ORDER_GREVLEX) { *why = "unknown ordering"; return false; }
+    if (ord < GC_ORDER_LEX || ord > GC_ORDER_BASIS) { *why = "unknown ordering"; return false; }
+    for (int j = 0; j < 32; ++j) p->basis[j] = p->inv[j] = 0;
+    if (ord == GC_ORDER_BASIS) {
+        if (!basis) { *why = "GC_ORDER_BASIS needs a basis"; return false; }
+        for (int j = 0; j < n; ++j) p->basis[j] = basis[j];
+        if (!invert_basis(n, p->basis, p->inv)) {
+            *why = "basis vectors are not linearly independent in F_2^n";
+            return false;
+        }
+    }
     if (w < -1 || w > n) { *why = "weight must be -1 or in [0, n]"; return false; }
     if (constraint != GC_CONSTRAINT_NONE && constraint != GC_CONSTRAINT_SELF_ORTHOGONAL) {
         *why = "unknown constraint";
@@ -48,8 +114,8 @@ bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why
     p->d = d;
     p->ord = ord;
     p->w = w;
-    p->filter = (w >= 0 && ord == GC_ORDER_GRAY);
-    p->N = (w < 0 || ord == GC_ORDER_GRAY) ? (1ull << n) : binom64(n, w);
+    p->filter = (w >= 0 && (ord == GC_ORDER_GRAY || ord == GC_ORDER_BASIS));
+    p->N = (w < 0 || ord == GC_ORDER_GRAY || ord == GC_ORDER_BASIS) ? (1ull << n) : binom64(n, w);
     p->valid = (w < 0) ? (1ull << n) : binom64(n, w);
     // sphere packing: radius floor((d-1)/2) balls around codewords are disjoint
     const int t = d >= 1 ? (d - 1) / 2 : 0;
@@ -172,8 +238,7 @@ static int make_batch(const gc_job* jobs, int njobs, std::vector<BatchJob>* out)
         const gc_job& J = jobs[j];
         BatchJob B{};
         std::string why;
-        if (!make_problem(J.prob.n, J.prob.d, J.prob.ordering, J.prob.weight, &B.p, &why,
-                          J.prob.constraint))
+        if (!make_problem(J.prob, &B.p, &why))
             return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": " + why);
         gc_plan_t in{};
         in.strategy = J.strategy;
@@ -214,6 +279,7 @@ const char* gc_last_error(void) { return g_last_error.c_str(); }
 uint64_t gc_candidate_count(int n, int w, int ordering) {
     HostProblem p;
     std::string why;
+    if (ordering == GC_ORDER_BASIS) ordering = GC_ORDER_GRAY;  // same rank space
     if (!make_problem(n, 2, ordering, w, &p, &why)) return 0;
     return p.N;
 }
@@ -229,8 +295,7 @@ int gc_plan(const gc_problem* prob, gc_plan_t* out) {
     if (!prob || !out) return fail(GC_ERR_INVALID, "null argument");
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
-        return fail(GC_ERR_INVALID, why);
+    if (!make_problem(*prob, &p, &why)) return fail(GC_ERR_INVALID, why);
     plan_for(p, out);
     return GC_OK;
 }
@@ -239,8 +304,7 @@ size_t gc_workspace_size(const gc_problem* prob, const gc_plan_t* plan) {
     if (!prob) return 0;
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
-        return 0;
+    if (!make_problem(*prob, &p, &why)) return 0;
     gc_plan_t pl;
     if (!resolve_plan(p, plan, &pl)) return 0;
     return single_workspace(p, pl, &why);
@@ -252,8 +316,7 @@ int gc_generate_async(const gc_problem* prob, const gc_plan_t* plan, uint32_t* d
     if (!prob || !d_stats || (!d_out && capacity > 0)) return fail(GC_ERR_INVALID, "null argument");
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
-        return fail(GC_ERR_INVALID, why);
+    if (!make_problem(*prob, &p, &why)) return fail(GC_ERR_INVALID, why);
     gc_plan_t pl;
     if (!resolve_plan(p, plan, &pl)) return fail(GC_ERR_INVALID, "bad strategy");
     return generate_async_impl(p, pl, d_out, capacity, d_stats, workspace, workspace_bytes,
@@ -338,6 +401,7 @@ int gc_unrank(int n, int ordering, int w, uint64_t rank0, uint64_t count, uint32
               void* stream) {
     HostProblem p;
     std::string why;
+    if (ordering == GC_ORDER_BASIS) return fail(GC_ERR_UNSUPPORTED, "gc_unrank: no basis argument");
     if (!make_problem(n, 2, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
     if (count > 0 && !d_vec) return fail(GC_ERR_INVALID, "null output");
     if (rank0 > p.N || count > p.N - rank0) return fail(GC_ERR_INVALID, "rank out of range");
@@ -348,6 +412,7 @@ int gc_rank(int n, int ordering, const uint32_t* d_vec, uint64_t count, uint64_t
             void* stream) {
     HostProblem p;
     std::string why;
+    if (ordering == GC_ORDER_BASIS) return fail(GC_ERR_UNSUPPORTED, "gc_rank: no basis argument");
     if (!make_problem(n, 2, ordering, -1, &p, &why)) return fail(GC_ERR_INVALID, why);
     if (count > 0 && (!d_vec || !d_rank)) return fail(GC_ERR_INVALID, "null pointer");
     return launch_rank(n, ordering, d_vec, count, d_rank, (cudaStream_t)stream);
@@ -389,6 +454,7 @@ int gc_bitmap_scan(int n, int ordering, int w, const uint32_t* d_bitmap, uint64_
                    void* stream) {
     HostProblem p;
     std::string why;
+    if (ordering == GC_ORDER_BASIS) return fail(GC_ERR_UNSUPPORTED, "gc_bitmap_scan: no basis argument");
     if (!make_problem(n, 2, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
     if (!d_found || (count && !d_bitmap) || (capacity && !d_out))
         return fail(GC_ERR_INVALID, "null pointer");

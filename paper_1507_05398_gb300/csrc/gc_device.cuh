@@ -78,7 +78,7 @@ __device__ __forceinline__ uint32_t gray_inverse(uint32_t g) {
 }
 
 // ---------------------------------------------------------------- orders
-enum : int { kLex = 0, kGray = 1, kGrlex = 2, kGrevlex = 3 };
+enum : int { kLex = 0, kGray = 1, kGrlex = 2, kGrevlex = 3, kBasis = 4 };
 
 // Everything the ordering maps need, small enough to pass by value.
 struct Order {
@@ -90,6 +90,10 @@ struct Order {
     uint64_t N;     // rank-space size
     // graded orders without a weight: cum[k] = number of vectors of weight < k
     uint64_t cum[kMaxN + 2];
+    // B-ordering (Section 4.3): basis[j] = b_{j+1}; inv[j] = row j of the
+    // inverse, so bit j of the rank of v is the parity of (v AND inv[j])
+    uint32_t basis[kMaxN];
+    uint32_t inv[kMaxN];
 };
 
 // Vector of rank r (r < N).  Returns false when the rank is skipped: a Gray
@@ -101,6 +105,10 @@ __device__ __forceinline__ bool unrank(const Order& o, const uint32_t (*C)[kMaxN
     bool ok = true;
     if (o.ord == kGray) {
         x = (uint32_t)(r ^ (r >> 1));
+        ok = !o.filter || __popc(x) == o.w;
+    } else if (o.ord == kBasis) {
+        x = 0;
+        for (uint64_t b = r; b; b &= b - 1) x ^= o.basis[__ffsll((long long)b) - 1];
         ok = !o.filter || __popc(x) == o.w;
     } else if (o.ord == kLex && o.w < 0) {
         x = (uint32_t)r;
@@ -134,6 +142,11 @@ __device__ __forceinline__ uint64_t rank_of(const Order& o, const uint32_t (*C)[
     switch (o.ord) {
         case kLex: return x;
         case kGray: return gray_inverse(x);
+        case kBasis: {
+            uint64_t r = 0;
+            for (int j = 0; j < n; ++j) r |= (uint64_t)(__popc(x & o.inv[j]) & 1) << j;
+            return r;
+        }
         default: {
             int k = __popc(x);
             uint64_t base = 0;

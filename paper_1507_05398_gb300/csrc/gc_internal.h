@@ -17,6 +17,8 @@ namespace gc {
 struct HostProblem {
     int n, d, ord, w;
     bool orth;         // self-orthogonal constraint (Section 4.4)
+    uint32_t basis[32];  // B-ordering basis and the rows of its inverse
+    uint32_t inv[32];
     bool filter;       // GRAY with a weight: ranks of the wrong weight skipped
     uint64_t N;        // rank-space size
     uint64_t valid;    // number of candidates (C(n,w) or 2^n)
@@ -25,7 +27,11 @@ struct HostProblem {
 
 uint64_t binom64(int n, int k);
 bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why,
-                  int constraint = GC_CONSTRAINT_NONE);
+                  int constraint = GC_CONSTRAINT_NONE, const uint32_t* basis = nullptr);
+// make_problem from the ABI struct
+bool make_problem(const gc_problem& q, HostProblem* out, std::string* why);
+// Fills an Order for the device from a checked problem.
+Order order_of(const HostProblem& p, bool filter, bool even);
 // Strategy and launch shape for a problem (gc_plan).
 void plan_for(const HostProblem& p, gc_plan_t* pl);
 

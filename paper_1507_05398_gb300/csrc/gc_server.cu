@@ -150,7 +150,7 @@ int gc_server_submit(gc_server* s, const gc_problem* prob, int strategy, uint64_
     if (!s || !prob || !request_id) return fail(GC_ERR_INVALID, "null argument");
     HostProblem p;
     std::string why;
-    if (!make_problem(prob->n, prob->d, prob->ordering, prob->weight, &p, &why, prob->constraint))
+    if (!make_problem(*prob, &p, &why))
         return fail(GC_ERR_INVALID, why);
     if (p.n > s->cfg.max_n) return fail(GC_ERR_UNSUPPORTED, "n above the server's max_n");
     // the persistent kernel may have left after an idle period: restart it

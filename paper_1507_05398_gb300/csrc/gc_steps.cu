@@ -21,21 +21,7 @@ __device__ void load_binom(uint32_t (*C)[kMaxN + 1]) {
     __syncthreads();
 }
 
-static Order make_order(const HostProblem& p, bool filter) {
-    Order o{};
-    o.n = p.n;
-    o.ord = p.ord;
-    o.w = p.w;
-    o.filter = filter;
-    o.even = false;
-    o.N = p.N;
-    uint64_t c = 0;
-    for (int k = 0; k <= kMaxN + 1; ++k) {
-        o.cum[k] = c;
-        if (k <= p.n) c += binom64(p.n, k);
-    }
-    return o;
-}
+static Order make_order(const HostProblem& p, bool filter) { return order_of(p, filter, false); }
 
 static int grid_for(uint64_t items, int per_block) {
     uint64_t g = (items + per_block - 1) / per_block;
@@ -82,10 +68,8 @@ int launch_rank(int n, int ord, const uint32_t* d_vec, uint64_t count, uint64_t*
                 cudaStream_t s) {
     if (count == 0) return GC_OK;
     HostProblem p{};
-    p.n = n;
-    p.ord = ord;
-    p.w = -1;
-    p.N = 1ull << n;
+    std::string why;
+    if (!make_problem(n, 2, ord, -1, &p, &why)) return fail(GC_ERR_INVALID, why);
     Order o = make_order(p, false);
     rank_kernel<<<grid_for(count, 256 * 16), 256, 0, s>>>(o, d_vec, count, d_rank);
     return check_launch("rank");

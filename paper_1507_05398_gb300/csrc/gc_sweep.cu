@@ -475,9 +475,11 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
 
             // resolve in order; identical in every CTA of the group
             uint64_t rt = 0;
-            const uint32_t nacc = block_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
-                                                job.orth != 0);
+            const uint32_t nacc =
+                job.orth ? block_resolve<true>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
+                                               s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr)
+                         : block_resolve<false>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
+                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr);
             if (lb == 0) resolve_tests += rt;
             mark_phase(6);
 
@@ -598,21 +600,7 @@ uint64_t high_ball_len(int n, int d) {
 // ------------------------------------------------------------------ host side
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-static Order make_order_host(const HostProblem& p) {
-    Order o{};
-    o.n = p.n;
-    o.ord = p.ord;
-    o.w = p.w;
-    o.filter = p.filter;
-    o.even = p.orth;
-    o.N = p.N;
-    uint64_t c = 0;
-    for (int k = 0; k <= kMaxN + 1; ++k) {
-        o.cum[k] = c;
-        if (k <= p.n) c += binom64(p.n, k);
-    }
-    return o;
-}
+static Order make_order_host(const HostProblem& p) { return order_of(p, p.filter, p.orth); }
 
 // Rough device cost of one job, used to balance jobs over groups.
 static double job_cost(const HostProblem& p, int strategy) {

@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "LEX", "GRAY", "GRLEX", "GREVLEX", "NO_WEIGHT", "ORDERS",
+    "LEX", "GRAY", "GRLEX", "GREVLEX", "BASIS", "NO_WEIGHT", "ORDERS",
     "CONSTRAINT_NONE", "CONSTRAINT_SELF_ORTHOGONAL",
     "STRATEGY_AUTO", "STRATEGY_DISTANCE", "STRATEGY_BITMAP",
     "GcError", "Problem", "Plan", "Stats", "lib", "library_path", "header_functions",
@@ -27,9 +27,9 @@ __all__ = [
     "ServerConfig", "Server",
 ]
 
-LEX, GRAY, GRLEX, GREVLEX = 0, 1, 2, 3
+LEX, GRAY, GRLEX, GREVLEX, BASIS = 0, 1, 2, 3, 4
 NO_WEIGHT = -1
-ORDERS = {"lex": LEX, "gray": GRAY, "grlex": GRLEX, "grevlex": GREVLEX}
+ORDERS = {"lex": LEX, "gray": GRAY, "grlex": GRLEX, "grevlex": GREVLEX, "basis": BASIS}
 STRATEGY_AUTO, STRATEGY_DISTANCE, STRATEGY_BITMAP = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -48,7 +48,8 @@ class GcError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("d", ctypes.c_int), ("ordering", ctypes.c_int),
-                ("weight", ctypes.c_int), ("constraint", ctypes.c_int)]
+                ("weight", ctypes.c_int), ("constraint", ctypes.c_int),
+                ("basis", ctypes.POINTER(ctypes.c_uint32))]
 
 
 CONSTRAINT_NONE, CONSTRAINT_SELF_ORTHOGONAL = 0, 1
@@ -160,6 +161,8 @@ def _check(rc: int, what: str):
 
 
 def _ord(o) -> int:
+    if isinstance(o, (list, tuple, np.ndarray)):
+        return BASIS
     return ORDERS[o] if isinstance(o, str) else int(o)
 
 
@@ -202,7 +205,14 @@ def _bound(n, d, weight, constraint):
 
 
 def _problem(n, d, ordering, weight, constraint=None):
-    return Problem(n, d, _ord(ordering), weight, _constraint(constraint))
+    """ordering: a name, an ordering code, or -- for a B-ordering (Section
+    4.3) -- the list of n basis vectors b_1..b_n."""
+    p = Problem(n, d, _ord(ordering), weight, _constraint(constraint), None)
+    if p.ordering == BASIS:
+        arr = (ctypes.c_uint32 * n)(*[int(v) for v in ordering])
+        p.basis = ctypes.cast(arr, ctypes.POINTER(ctypes.c_uint32))
+        p._basis_keepalive = arr
+    return p
 
 
 def plan(n: int, d: int, ordering="lex", weight: int = NO_WEIGHT, constraint=None) -> Plan:

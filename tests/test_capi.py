@@ -29,7 +29,7 @@ def test_strerror_names_every_code():
 @pytest.mark.parametrize("n,w,ordname,want", [
     (10, -1, "lex", 1024), (32, -1, "gray", 1 << 32), (12, 5, "lex", comb(12, 5)),
     (12, 5, "grevlex", comb(12, 5)), (12, 5, "gray", 4096), (0, -1, "lex", 0), (33, -1, "lex", 0),
-    (5, 6, "lex", 0), (5, -2, "lex", 0), (5, -1, 4, 0)])
+    (5, 6, "lex", 0), (5, -2, "lex", 0), (5, -1, 5, 0), (5, -1, 4, 32), (6, 3, 4, 64)])
 def test_candidate_count(n, w, ordname, want):
     assert G.candidate_count(n, w, ordname) == want
 
