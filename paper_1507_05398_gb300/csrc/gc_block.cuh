@@ -184,6 +184,7 @@ __device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, uint32_t* x, 
 //   x/off[0..n)   candidates in order (modified: compacted)
 //   acc/acc_off   receives accepted vectors/offsets in order (capacity >= n)
 //   Mt            kResolveWords x kResolveBlock words of shared memory
+// block (<= kResolveBlock) sets how many entries one conflict matrix takes.
 // Returns the number accepted.
 // tim (optional, thread 0 only): cycles added to tim[0] matrix build,
 // tim[1] rounds, tim[2] append and kill step; tim[3] counts rounds.
@@ -192,7 +193,8 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
                                                   uint8_t* dead, uint32_t n, int d,
                                                   uint32_t* acc, uint32_t* acc_off,
                                                   uint32_t (*Mt)[kResolveBlock], uint64_t& nt,
-                                                  unsigned long long* tim = nullptr) {
+                                                  unsigned long long* tim = nullptr,
+                                                  uint32_t block = kResolveBlock) {
     constexpr bool orth = kOrth;
     const int lane = lane_id(), warp = warp_id();
     const bool timing = tim && threadIdx.x == 0;
@@ -215,7 +217,7 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
     uint32_t nacc = 0;
     uint32_t start = 0, end = n;
     while (start < end) {
-        const uint32_t P = min((uint32_t)kResolveBlock, end - start);
+        const uint32_t P = min(block, end - start);
         const uint32_t nwords = (P + 31u) / 32u;
         const uint32_t* bx = x + start;
         // conflict matrix, strictly lower triangle, stored transposed

@@ -160,6 +160,9 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
         pl->strategy = GC_STRATEGY_BITMAP;
     else
         pl->strategy = GC_STRATEGY_DISTANCE;
+    // bitmap windows carry no old-code scan, so larger windows (more
+    // survivors per group exchange) pay off there (measured on GB300)
+    if (pl->strategy == GC_STRATEGY_BITMAP) pl->survivor_target = 512;
     if (const char* e = std::getenv("GC_STRATEGY")) {
         if (!std::strcmp(e, "distance")) pl->strategy = GC_STRATEGY_DISTANCE;
         if (!std::strcmp(e, "bitmap")) pl->strategy = GC_STRATEGY_BITMAP;
@@ -169,7 +172,10 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
 static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* out) {
     plan_for(p, out);
     if (in) {
-        if (in->strategy != GC_STRATEGY_AUTO && !p.orth) out->strategy = in->strategy;
+        if (in->strategy != GC_STRATEGY_AUTO && !p.orth) {
+            out->strategy = in->strategy;
+            out->survivor_target = in->strategy == GC_STRATEGY_BITMAP ? 512 : 256;
+        }
         if (in->grid > 0) out->grid = in->grid;
         if (in->window_min) out->window_min = in->window_min;
         if (in->window_max) out->window_max = in->window_max;

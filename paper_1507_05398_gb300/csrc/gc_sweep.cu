@@ -78,6 +78,7 @@ struct BatchArgs {
     unsigned* err;
     uint32_t cache_words;
     long long timeout_cycles;
+    uint32_t resolve_block;       // entries per conflict matrix (<= kResolveBlock)
     ServeQueue queue;             // used when queue.descs != nullptr
 };
 
@@ -477,9 +478,11 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             uint64_t rt = 0;
             const uint32_t nacc =
                 job.orth ? block_resolve<true>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                               s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr)
+                                               s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
+                                               a.resolve_block)
                          : block_resolve<false>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr);
+                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
+                                                a.resolve_block);
             if (lb == 0) resolve_tests += rt;
             mark_phase(6);
 
@@ -601,6 +604,15 @@ uint64_t high_ball_len(int n, int d) {
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 static Order make_order_host(const HostProblem& p) { return order_of(p, p.filter, p.orth); }
+
+// Entries per resolver conflict matrix: smaller blocks build smaller
+// matrices but take more block steps.  GC_RESOLVE_BLOCK overrides (tuning).
+static uint32_t resolve_block_size() {
+    uint32_t b = 256;
+    if (const char* e = std::getenv("GC_RESOLVE_BLOCK")) b = (uint32_t)std::atoi(e);
+    b = (b + 31u) & ~31u;
+    return std::max<uint32_t>(32u, std::min<uint32_t>(b, kResolveBlock));
+}
 
 // Rough device cost of one job, used to balance jobs over groups.
 static double job_cost(const HostProblem& p, int strategy) {
@@ -844,6 +856,7 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
     a.err = reinterpret_cast<unsigned*>(ws + L.off_err);
     a.cache_words = L.cache_words;
     a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
+    a.resolve_block = resolve_block_size();
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(L.grid), dim3(kBlock), args,
                                     L.smem_bytes, stream);
@@ -948,7 +961,7 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
     D->out = d_out;
     D->cap = cap;
     D->stats = d_stats;
-    D->target = 256;
+    D->target = D->strategy == kStratBitmap ? 512 : 256;
     D->wmax = (uint32_t)((uint64_t)L.group_ctas * kChunk);
     D->wmin = std::min<uint32_t>(256, D->wmax);
     if (D->strategy == kStratBitmap && p.d >= 1) {
@@ -1029,6 +1042,7 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
     a.err = reinterpret_cast<unsigned*>(ws + L.off_err);
     a.cache_words = L.cache_words;
     a.timeout_cycles = 20000000000ll;
+    a.resolve_block = resolve_block_size();
     int dev = 0, clk_khz = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
