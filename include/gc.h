@@ -162,6 +162,20 @@ uint64_t gc_capacity_bound(int n, int d, int weight_or_none);
  * or GC_ERR_INVALID. */
 int gc_plan(const gc_problem *prob, gc_plan_t *out_plan);
 
+/* Measured choice: runs the candidate plans (distance or bitmap strategy,
+ * survivor targets 256/512/1024, all / a quarter / an eighth of the SMs) for
+ * this problem on the current device, returns the fastest in *best and its
+ * time in *best_ms (may be NULL), and appends it to the tuning cache if one
+ * is installed.  Synchronous; allocates its own scratch.  GC_ORDER_BASIS
+ * problems are tuned but not cached (the basis is not part of the key). */
+int gc_autotune(const gc_problem *prob, gc_plan_t *best, double *best_ms);
+
+/* Installs a plain-text tuning cache file (NULL or "" removes it; default:
+ * the GC_TUNE_CACHE environment variable).  While installed, gc_plan() and
+ * every entry point that plans by itself use the cached plan of a problem
+ * (key: n, d, ordering, weight, constraint, device name; last entry wins). */
+int gc_set_tune_cache(const char *path);
+
 /* ---- the whole sweep ---------------------------------------------------- */
 
 /* Device bytes of scratch gc_generate_async() needs for this problem and

@@ -170,7 +170,7 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
 }
 
 static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* out) {
-    plan_for(p, out);
+    if (!tuned_plan(p, out)) plan_for(p, out);
     if (in) {
         if (in->strategy != GC_STRATEGY_AUTO && !p.orth) {
             out->strategy = in->strategy;
@@ -302,7 +302,7 @@ int gc_plan(const gc_problem* prob, gc_plan_t* out) {
     HostProblem p;
     std::string why;
     if (!make_problem(*prob, &p, &why)) return fail(GC_ERR_INVALID, why);
-    plan_for(p, out);
+    if (!tuned_plan(p, out)) plan_for(p, out);
     return GC_OK;
 }
 

@@ -34,6 +34,8 @@ bool make_problem(const gc_problem& q, HostProblem* out, std::string* why);
 Order order_of(const HostProblem& p, bool filter, bool even);
 // Strategy and launch shape for a problem (gc_plan).
 void plan_for(const HostProblem& p, gc_plan_t* pl);
+// The plan the installed tuning cache holds for a problem, if any (gc_tune.cu).
+bool tuned_plan(const HostProblem& p, gc_plan_t* out);
 
 // Word-grouped ball: entries (e_high << 3) | radius for every high part of
 // weight <= d-1 over the n-5 word-index bits; radius = d-1-weight(e_high),

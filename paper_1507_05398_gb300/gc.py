@@ -24,7 +24,7 @@ __all__ = [
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
     "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
     "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
-    "ServerConfig", "Server",
+    "ServerConfig", "Server", "autotune", "set_tune_cache",
 ]
 
 LEX, GRAY, GRLEX, GREVLEX, BASIS = 0, 1, 2, 3, 4
@@ -117,6 +117,9 @@ _SIGS = {
     "gc_server_fetch": (_i32, [_vp, _u64, _vp, ctypes.POINTER(_u64), ctypes.c_void_p]),
     "gc_server_release": (_i32, [_vp, _u64]),
     "gc_server_destroy": (_i32, [_vp]),
+    "gc_autotune": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan),
+                           ctypes.POINTER(ctypes.c_double)]),
+    "gc_set_tune_cache": (_i32, [ctypes.c_char_p]),
     "gc_batch_generate_async": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp]),
     "gc_noalloc_scratch_bytes": (ctypes.c_size_t, []),
 }
@@ -509,3 +512,16 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def autotune(n, d, ordering="lex", weight=NO_WEIGHT, constraint=None):
+    """(fastest Plan measured on this device, its time in ms)."""
+    best, ms = Plan(), ctypes.c_double(0)
+    _check(lib().gc_autotune(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
+                             ctypes.byref(best), ctypes.byref(ms)), "gc_autotune")
+    return best, ms.value
+
+
+def set_tune_cache(path):
+    """Install (or with None remove) the plain-text tuning cache."""
+    _check(lib().gc_set_tune_cache(path.encode() if path else None), "gc_set_tune_cache")
