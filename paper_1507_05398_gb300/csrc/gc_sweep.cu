@@ -113,6 +113,7 @@ struct __align__(16) SweepSmem {
     uint32_t C[kMaxN + 1][kMaxN + 1];
     uint32_t pad0[3];
     uint32_t lowball[8][32];  // lowball[r][c]: bits y < 32 with popc(y ^ c) <= r
+    uint32_t lowlight[8];     // lowlight[k]: bits y < 32 with popc(y) < k (k >= 6: all)
     __align__(16) uint32_t list_x[kChunk];
     __align__(16) uint32_t list_off[kChunk];
     __align__(16) uint32_t accA[kSurvCap];
@@ -286,6 +287,12 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     if (__popc((unsigned)(y ^ c)) <= r) m |= 1u << y;
                 s.lowball[r][c] = m;
             }
+            for (int k = tid; k < 8; k += kBlock) {
+                uint32_t m = 0;
+                for (int y = 0; y < (1 << nl); ++y)
+                    if (__popc((unsigned)y) < k) m |= 1u << y;
+                s.lowlight[k] = m;
+            }
         }
         // job start: clear this CTA's share of the bitmap
         if (job.strategy == kStratBitmap) {
@@ -346,6 +353,10 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                         if (word == cw) mask &= ~((2u << (c & 31u)) - 1u);
                     } else if (o.ord == kGray) {
                         skip = gray_inverse(word) < gray_inverse(cw);
+                    } else if (o.ord == kGrlex || o.ord == kGrevlex) {
+                        // graded orders: every vector lighter than c is behind it
+                        const int below = __popc(c) - __popc(word);  // low bits must weigh >= this
+                        if (below > 0) mask &= ~s.lowlight[below < 7 ? below : 7];
                     }
                     if (!skip && mask) {
                         atomicOr(grp.bitmap + word, mask);
