@@ -306,7 +306,8 @@ def run_ours(args):
         "windows_per_step": sum(st.windows for st in stats_now),
         "survivors_per_step": sum(st.survivors for st in stats_now),
         "phase_ms_cta0": {f"n={n} d={d} {o}": dict(
-            {ph: round(1e3 * c / clock_hz, 4) for ph, c in zip(G.Stats.PHASES, st.phase_cycles)},
+            {ph: (c if ph in ("rounds", "blocks") else round(1e3 * c / clock_hz, 4))
+             for ph, c in zip(G.Stats.PHASES, st.phase_cycles)},
             windows=st.windows, survivors=st.survivors)
             for (n, d, o, w), st in zip(probs, stats_now)},
         "e2e": {"value": e2e_value, "unit": "tests/s", "h2d_bytes_per_step": 0,

@@ -28,6 +28,10 @@ Parity status of each function (the pins are in ``tests/test_oracle.py``):
   ball_mark / scan           whole order equals O1; the greedy code's balls
                              cover every candidate; scan of an empty map is the
                              order itself)
+  order_list64 / greedy64 /  pinned (equal to the 32-bit forms for n <= 12; the
+  verify64 (n <= 64)         disjoint-block closed form of constant-weight codes
+                             with d = 2w at n = 33..64 in all four orders; O3
+                             accepts the output and rejects perturbations)
 """
 from __future__ import annotations
 
@@ -91,6 +95,14 @@ def _load():
             lib.orc_resolve.argtypes = [i32, u32p, i64, i64p]
             lib.orc_ball_mark.restype = i32
             lib.orc_ball_mark.argtypes = [i32, i32, u32p, i64, u32p]
+            lib.orc64_candidate_count.restype = ctypes.c_uint64
+            lib.orc64_candidate_count.argtypes = [i32, i32]
+            lib.orc64_order_list.restype = i64
+            lib.orc64_order_list.argtypes = [i32, i32, i32, u32p, i64]
+            lib.orc64_greedy.restype = i64
+            lib.orc64_greedy.argtypes = [i32, i32, i32, i32, i32, u32p, i64p, i64]
+            lib.orc64_verify.restype = i32
+            lib.orc64_verify.argtypes = [i32, i32, i32, i32, u32p, i64]
             lib.orc_scan.restype = i64
             lib.orc_scan.argtypes = [i32, i32, i32, u32p, ctypes.c_uint64, ctypes.c_uint64,
                                      u32p, i64]
@@ -231,3 +243,39 @@ def dense_tests(positions: np.ndarray, n_candidates: int) -> int:
     candidate, so the total is the sum over codewords of (N - 1 - p)."""
     p = np.asarray(positions, dtype=np.int64)
     return int((n_candidates - 1 - p).sum())
+
+
+# ---- vectors of up to 64 coordinates (uint64 words) -----------------------
+def candidate_count64(n: int, w: int = -1) -> int:
+    return int(_load().orc64_candidate_count(n, w))
+
+
+def order_list64(n: int, ordering, w: int = -1) -> np.ndarray:
+    """Candidates in order, by sorting the candidate set with the order's
+    comparator (Section 4.2 orders, n <= 64)."""
+    cnt = candidate_count64(n, w)
+    out = np.empty(max(cnt, 1), dtype=np.uint64)
+    k = _load().orc64_order_list(n, _ord(ordering), w, _ptr(out), cnt)
+    if k != cnt:
+        raise RuntimeError(f"order_list64 returned {k}, expected {cnt}")
+    return out[:cnt].copy()
+
+
+def greedy64(n: int, d: int, ordering="lex", w: int = -1, orth: bool = False,
+             with_pos: bool = False):
+    """The greedy of Section 3 for n <= 64 (orth: with the Section 4.4
+    constraint), pairwise over the sorted candidate list."""
+    cap = max(min(candidate_count64(n, w), 1 << 26), 1)
+    out = np.empty(cap, dtype=np.uint64)
+    pos = np.empty(cap, dtype=np.int64) if with_pos else None
+    k = _load().orc64_greedy(n, d, _ord(ordering), w, int(bool(orth)), _ptr(out),
+                             _ptr(pos) if with_pos else None, cap)
+    if k < 0:
+        raise RuntimeError(f"oracle error {k} for n={n} d={d} ord={ordering} w={w}")
+    return (out[:k].copy(), pos[:k].copy()) if with_pos else out[:k].copy()
+
+
+def verify64(n: int, d: int, ordering, w: int, L) -> int:
+    """O3 for n <= 64: 0 iff L is exactly the greedy output."""
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.uint64))
+    return int(_load().orc64_verify(n, d, _ord(ordering), w, _ptr(L), len(L)))

@@ -494,3 +494,161 @@ int64_t orc_greedy_border(int n, int d, const uint32_t *basis, int w, uint32_t *
     free(C);
     return size;
 }
+
+/* ---- vectors of up to 64 coordinates ------------------------------------ */
+/* The same greedy for 1 <= n <= 64 (Section 3; the constant-weight codes of
+ * Section 7 go to length 35).  Vectors are the low n bits of a uint64 with
+ * coordinate 1 the most significant of them.  These forms materialise the
+ * candidate list by the definition of the order: every candidate (the
+ * weight-w vectors, or all 2^n vectors) sorted with the order's comparator.
+ * n = 64 needs a weight (2^64 candidates do not fit a count).  orth = 1 adds
+ * the Section 4.4 constraint (even weight, even inner product with every
+ * earlier codeword). */
+static uint64_t pascal64[65][65];
+static int pascal64_ready = 0;
+static uint64_t binom64c(int n, int k) {
+    if (!pascal64_ready) {
+        for (int p = 0; p <= 64; ++p)
+            for (int q = 0; q <= 64; ++q)
+                pascal64[p][q] = (q == 0) ? 1 : (p == 0 ? 0 : pascal64[p - 1][q - 1] + pascal64[p - 1][q]);
+        pascal64_ready = 1;
+    }
+    if (n < 0 || k < 0 || k > n || n > 64) return 0;
+    return pascal64[n][k];
+}
+
+static int valid_args64(int n, int ord, int w) {
+    if (n < 1 || n > 64) return 0;
+    if (ord < ORC_LEX || ord > ORC_GREVLEX) return 0;
+    if (w < -1 || w > n) return 0;
+    if (n == 64 && w < 0) return 0;
+    return 1;
+}
+
+uint64_t orc64_candidate_count(int n, int w) {
+    if (n < 1 || n > 64 || w < -1 || w > n || (n == 64 && w < 0)) return 0;
+    return w < 0 ? (1ull << n) : binom64c(n, w);
+}
+
+static int popc64(uint64_t v) { return __builtin_popcountll(v); }
+
+static uint64_t gray_rank64(uint64_t g) { /* r with r ^ (r >> 1) == g */
+    uint64_t r = 0;
+    for (uint64_t s = g; s; s >>= 1) r ^= s;
+    return r;
+}
+static int cmp64_lex(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+static int cmp64_gray(const void *a, const void *b) {
+    uint64_t x = gray_rank64(*(const uint64_t *)a), y = gray_rank64(*(const uint64_t *)b);
+    return (x > y) - (x < y);
+}
+static int cmp64_grlex(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    int wx = popc64(x), wy = popc64(y);
+    if (wx != wy) return wx - wy;
+    return (x > y) - (x < y);
+}
+static int cmp64_grevlex(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    int wx = popc64(x), wy = popc64(y);
+    if (wx != wy) return wx - wy;
+    if (x == y) return 0;
+    /* the last coordinate where they differ is the lowest differing bit; the
+     * vector holding the 1 there comes first */
+    for (int i = 0; i < 64; ++i) {
+        uint64_t m = 1ull << i;
+        if ((x ^ y) & m) return (x & m) ? -1 : 1;
+    }
+    return 0;
+}
+
+/* Candidates of (n, ord, w) in order, by sorting the candidate set with the
+ * order's comparator.  Returns the count, or ORC_EINVAL / ORC_ENOMEM (also
+ * when the count exceeds cap). */
+int64_t orc64_order_list(int n, int ord, int w, uint64_t *out, int64_t cap) {
+    if (!valid_args64(n, ord, w)) return ORC_EINVAL;
+    uint64_t cnt = orc64_candidate_count(n, w);
+    if (cnt > (uint64_t)cap) return ORC_ENOMEM;
+    int64_t k = 0;
+    if (w < 0) {
+        for (uint64_t v = 0; v < cnt; ++v) out[k++] = v;
+    } else if (w == 0) {
+        out[k++] = 0;
+    } else {
+        /* every weight-w pattern once: Gosper's rule from the smallest */
+        uint64_t y = (w == 64) ? ~0ull : ((1ull << w) - 1);
+        for (uint64_t i = 0; i < cnt; ++i) {
+            out[k++] = y;
+            if (i + 1 < cnt) {
+                uint64_t c = y & (~y + 1), r = y + c;
+                y = (((r ^ y) >> 2) / c) | r;
+            }
+        }
+    }
+    int (*cmp)(const void *, const void *) =
+        ord == ORC_LEX ? cmp64_lex : ord == ORC_GRAY ? cmp64_gray
+        : ord == ORC_GRLEX ? cmp64_grlex : cmp64_grevlex;
+    qsort(out, (size_t)k, sizeof(uint64_t), cmp);
+    return k;
+}
+
+/* The greedy of Section 3 (orth = 1: with the Section 4.4 constraint),
+ * pairwise, over the sorted candidate list.  Writes up to cap codewords and
+ * their candidate indices; returns |C|. */
+int64_t orc64_greedy(int n, int d, int ord, int w, int orth, uint64_t *out, int64_t *pos,
+                     int64_t cap) {
+    if (!valid_args64(n, ord, w) || d < 0) return ORC_EINVAL;
+    uint64_t cnt = orc64_candidate_count(n, w);
+    if (cnt > (1ull << 28)) return ORC_ENOMEM;
+    uint64_t *cand = (uint64_t *)malloc((cnt ? cnt : 1) * sizeof(uint64_t));
+    uint64_t *C = (uint64_t *)malloc((cnt ? cnt : 1) * sizeof(uint64_t));
+    if (!cand || !C) { free(cand); free(C); return ORC_ENOMEM; }
+    int64_t m = orc64_order_list(n, ord, w, cand, (int64_t)cnt);
+    if (m < 0) { free(cand); free(C); return m; }
+    int64_t size = 0;
+    for (int64_t idx = 0; idx < m; ++idx) {
+        uint64_t x = cand[idx];
+        int ok = !orth || (popc64(x) % 2) == 0;
+        for (int64_t j = 0; ok && j < size; ++j) {
+            if (popc64(x ^ C[j]) < d) ok = 0;
+            if (orth && (popc64(x & C[j]) % 2) != 0) ok = 0;
+        }
+        if (ok) {
+            if (size < cap) { out[size] = x; if (pos) pos[size] = idx; }
+            C[size++] = x;
+        }
+    }
+    free(cand);
+    free(C);
+    return size;
+}
+
+/* O3 for up to 64 coordinates (no constraint): 0 iff L[0..len) is exactly
+ * the greedy output; the codes are those of orc_verify. */
+int orc64_verify(int n, int d, int ord, int w, const uint64_t *L, int64_t len) {
+    if (!valid_args64(n, ord, w)) return 1;
+    for (int64_t i = 0; i < len; ++i)
+        for (int64_t j = 0; j < i; ++j)
+            if (popc64(L[i] ^ L[j]) < d) return 2;
+    uint64_t cnt = orc64_candidate_count(n, w);
+    if (cnt > (1ull << 28)) return 4;
+    uint64_t *cand = (uint64_t *)malloc((cnt ? cnt : 1) * sizeof(uint64_t));
+    if (!cand) return 4;
+    int64_t m = orc64_order_list(n, ord, w, cand, (int64_t)cnt);
+    int64_t i = 0;
+    int rc = 0;
+    for (int64_t q = 0; q < m && rc == 0; ++q) {
+        uint64_t x = cand[q];
+        if (i < len && L[i] == x) { ++i; continue; }
+        int covered = 0;
+        for (int64_t j = 0; j < i; ++j)
+            if (popc64(x ^ L[j]) <= d - 1) { covered = 1; break; }
+        if (!covered) rc = 3;
+    }
+    free(cand);
+    if (rc) return rc;
+    return i == len ? 0 : 1;
+}
