@@ -11,7 +11,9 @@
  *
  * Conventions shared by every entry point:
  *  - A length-n vector is the low n bits of a uint32_t, coordinate 1 in the
- *    most significant of those bits ("011" is 3).  1 <= n <= 32.
+ *    most significant of those bits ("011" is 3).  1 <= n <= 32, except for
+ *    the wide entry points (gc_*64), whose vectors are the low n bits of a
+ *    uint64_t with 1 <= n <= 64.
  *  - Orderings (the paper names them but defines none; these are the readings):
  *      GC_ORDER_LEX      ascending integer (Example 1 of Section 4.1).
  *      GC_ORDER_GRAY     binary-reflected Gray code: rank r -> r ^ (r >> 1).
@@ -22,9 +24,10 @@
  *  - Constant weight: weight_or_none in [0, n] keeps only weight-w vectors, in
  *    the same relative order; GC_NO_WEIGHT (-1) keeps all 2^n vectors.
  *  - "Rank space" of a problem: 2^n ranks when no weight is given or the
- *    order is GRAY or BASIS (ranks of the wrong weight are skipped); C(n, w)
- *    ranks for LEX, GRLEX and GREVLEX with a weight (LEX and GRLEX restricted
- *    to one weight are the same sequence).
+ *    order is BASIS (B-ordering ranks of the wrong weight are skipped);
+ *    C(n, w) ranks for LEX, GRAY, GRLEX and GREVLEX with a weight: rank i is
+ *    the i-th weight-w vector of the order, found in closed form (LEX and
+ *    GRLEX restricted to one weight are the same sequence).
  *  - Return value: GC_OK (0) or a positive GC_ERR_* code; no exception or
  *    abort crosses the ABI.  gc_strerror() names the code; gc_last_error()
  *    returns a one-line message about the most recent failure on the calling
@@ -55,7 +58,7 @@ typedef enum {
     GC_ORDER_GREVLEX = 3,
     /* Section 4.3: the B-ordering of an ordered basis b_1..b_n of F_2^n --
      * rank r is the XOR of the b_j over the set bits j-1 of r (0, b_1, b_2,
-     * b_2+b_1, b_3, ...).  Needs gc_problem.basis; rank space as for GRAY. */
+     * b_2+b_1, b_3, ...).  Needs gc_problem.basis; 2^n ranks. */
     GC_ORDER_BASIS = 4
 } gc_ordering;
 
@@ -91,7 +94,7 @@ enum {
 
 /* One problem instance. */
 typedef struct {
-    int n;              /* code length, 1..32 */
+    int n;              /* code length, 1..32 (1..64 for the gc_*64 entries) */
     int d;              /* minimum distance, >= 0 (d <= 1 accepts all) */
     int ordering;       /* gc_ordering */
     int weight;         /* GC_NO_WEIGHT or 0..n */
@@ -116,7 +119,7 @@ typedef struct {
     uint64_t codewords;        /* |C| (the true size even past capacity) */
     uint64_t candidates;       /* candidates swept (rank-space size) */
     uint64_t dense_tests;      /* sum over candidates of |C before it|
-                                  (0 when ranks are skipped: GRAY with a
+                                  (0 when ranks are skipped: BASIS with a
                                   weight, self-orthogonal problems) */
     uint64_t executed_tests;   /* distance tests the kernels executed */
     uint64_t marks;            /* bitmap words OR-ed by ball marking */
@@ -142,7 +145,8 @@ const char *gc_strerror(int err);
 /* One-line description of the last failure on this thread ("" if none). */
 const char *gc_last_error(void);
 
-/* Rank-space size of a problem (see "Rank space" above), 0 if invalid. */
+/* Rank-space size of a problem (see "Rank space" above), n <= 64; 0 if
+ * invalid or not representable (2^64 ranks at n = 64). */
 uint64_t gc_candidate_count(int n, int weight_or_none, int ordering);
 
 /* An upper bound on |C| that is always safe as an output capacity:
@@ -150,8 +154,8 @@ uint64_t gc_candidate_count(int n, int weight_or_none, int ordering);
  * floor(2^n / V(n, floor((d-1)/2)))) -- the radius-floor((d-1)/2) balls
  * around codewords are disjoint.  (A self-orthogonal code also has at most
  * 2^floor(n/2) words: its span is a self-orthogonal linear code; the
- * problem-struct entry points use that too.)  Returns 0 for invalid
- * arguments. */
+ * problem-struct entry points use that too.)  n <= 64.  Returns 0 for
+ * invalid arguments. */
 uint64_t gc_capacity_bound(int n, int d, int weight_or_none);
 
 /* Choose a strategy and launch shape for a problem on the current device.
@@ -204,6 +208,25 @@ int gc_generate(int n, int d, int ordering, int weight_or_none,
 int gc_generate_async(const gc_problem *prob, const gc_plan_t *plan,
                       uint32_t *d_out, uint64_t capacity, gc_stats *d_stats,
                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- wide vectors: 1 <= n <= 64, uint64_t words ------------------------- */
+/* The same sweep for codes longer than 32 (Section 7 builds constant-weight
+ * codes up to length 35).  Vectors are the low n bits of a uint64_t,
+ * coordinate 1 the most significant of them.  Orders LEX, GRAY, GRLEX and
+ * GREVLEX, with or without a weight, and the self-orthogonal constraint;
+ * GC_ORDER_BASIS is not supported here (GC_ERR_INVALID).  n = 64 needs a
+ * weight (the rank space must fit a uint64).  The
+ * distance strategy only: an explicit GC_STRATEGY_BITMAP plan gives
+ * GC_ERR_UNSUPPORTED (0 from gc_workspace_size64), AUTO takes DISTANCE.
+ * Problems with n <= 32 are accepted too and give the same code as the
+ * narrow entries, zero-extended.  Arguments, ownership and errors are those
+ * of the narrow forms, with words of 8 bytes. */
+size_t gc_workspace_size64(const gc_problem *prob, const gc_plan_t *plan);
+int gc_generate64(int n, int d, int ordering, int weight_or_none,
+                  uint64_t *out_codewords, uint64_t *inout_count);
+int gc_generate64_async(const gc_problem *prob, const gc_plan_t *plan,
+                        uint64_t *d_out, uint64_t capacity, gc_stats *d_stats,
+                        void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---- batches: many codes in one launch --------------------------------- */
 
@@ -304,15 +327,30 @@ int gc_generate_noalloc(const gc_problem *prob, const gc_plan_t *plan,
 /* Size in bytes of gc_generate_noalloc's static scratch array. */
 size_t gc_noalloc_scratch_bytes(void);
 
+/* ---- Cartesian product of codes (Section 5, "Recursion in Self
+ *      orthogonal codes") --------------------------------------------------- */
+/* d_out[i * nb + j] = (d_a[i] << len_b) | d_b[j] for i < na, j < nb: every
+ * codeword of A (length len_a) followed by every codeword of B (length
+ * len_b), A's words outermost.  The product of two self-orthogonal codes is
+ * self-orthogonal and its distance is the smaller of the two; Section 5
+ * builds Code[n, d] from the greedy Code[n - k, d] and Code[k, d] this way
+ * (its example: the self-orthogonal [8, 4] code with Code[4, 4] gives a
+ * length-12 code of distance 4).  Device pointers, stream-ordered.
+ * Errors: GC_ERR_INVALID unless 1 <= len_a, 1 <= len_b and len_a + len_b <=
+ * 32 (gc_product) or 64 (gc_product64), or on a null pointer with a nonzero
+ * count; GC_ERR_CAPACITY (nothing written) if capacity < na * nb. */
+int gc_product(const uint32_t *d_a, uint64_t na, int len_a, const uint32_t *d_b,
+               uint64_t nb, int len_b, uint32_t *d_out, uint64_t capacity, void *stream);
+int gc_product64(const uint64_t *d_a, uint64_t na, int len_a, const uint64_t *d_b,
+                 uint64_t nb, int len_b, uint64_t *d_out, uint64_t capacity, void *stream);
+
 /* ---- the steps of the sweep, callable one at a time (for tests and for
  *      callers composing their own pipeline) ------------------------------ */
 
 /* Step 1, ordering (Section 4.2): d_vectors[i] = the candidate of rank
- * rank0 + i, for i < count, in the problem's rank space.  For GRAY with a
- * weight the ranks index the full 2^n Gray sequence and the weight is not
- * applied here (the sweep skips vectors of the wrong weight).  Device
- * pointer; rank0 + count must not exceed the rank-space size
- * (GC_ERR_INVALID otherwise). */
+ * rank0 + i, for i < count, in the problem's rank space (with a weight: the
+ * weight-w vectors in order).  Device pointer; rank0 + count must not exceed
+ * the rank-space size (GC_ERR_INVALID otherwise). */
 int gc_unrank(int n, int ordering, int weight_or_none, uint64_t rank0,
               uint64_t count, uint32_t *d_vectors, void *stream);
 

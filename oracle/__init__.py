@@ -28,6 +28,10 @@ Parity status of each function (the pins are in ``tests/test_oracle.py``):
   ball_mark / scan           whole order equals O1; the greedy code's balls
                              cover every candidate; scan of an empty map is the
                              order itself)
+  product64                  pinned (the example of Section 5: the self-orthogonal
+                             [8,4] code times Code[4,4] is a self-orthogonal
+                             [12,5,4] code; brute-force minimum distance of
+                             products of small random codes)
   order_list64 / greedy64 /  pinned (equal to the 32-bit forms for n <= 12; the
   verify64 (n <= 64)         disjoint-block closed form of constant-weight codes
                              with d = 2w at n = 33..64 in all four orders; O3
@@ -103,6 +107,8 @@ def _load():
             lib.orc64_greedy.argtypes = [i32, i32, i32, i32, i32, u32p, i64p, i64]
             lib.orc64_verify.restype = i32
             lib.orc64_verify.argtypes = [i32, i32, i32, i32, u32p, i64]
+            lib.orc64_product.restype = i64
+            lib.orc64_product.argtypes = [u32p, i64, u32p, i64, i32, i32, u32p, i64]
             lib.orc_scan.restype = i64
             lib.orc_scan.argtypes = [i32, i32, i32, u32p, ctypes.c_uint64, ctypes.c_uint64,
                                      u32p, i64]
@@ -279,3 +285,17 @@ def verify64(n: int, d: int, ordering, w: int, L) -> int:
     """O3 for n <= 64: 0 iff L is exactly the greedy output."""
     L = np.ascontiguousarray(np.asarray(L, dtype=np.uint64))
     return int(_load().orc64_verify(n, d, _ord(ordering), w, _ptr(L), len(L)))
+
+
+def product64(A, B, len_a: int, len_b: int) -> np.ndarray:
+    """Cartesian product of two codes (Section 5, recursion for
+    self-orthogonal codes): (a << len_b) | b for every a in A (outer) and b
+    in B (inner)."""
+    a = np.ascontiguousarray(np.asarray(A, dtype=np.uint64))
+    b = np.ascontiguousarray(np.asarray(B, dtype=np.uint64))
+    out = np.empty(max(len(a) * len(b), 1), dtype=np.uint64)
+    k = _load().orc64_product(_ptr(a), len(a), _ptr(b), len(b), len_a, len_b, _ptr(out),
+                              len(out))
+    if k < 0:
+        raise RuntimeError("product: words do not fit 64 bits")
+    return out[:k].copy()

@@ -373,36 +373,23 @@ int orc_ball_mark(int n, int d, const uint32_t *code, int64_t nk, uint32_t *bitm
 }
 
 /* Find-unmarked scan over ranks [rank0, rank0 + count) of the rank space:
- * 2^n ranks with no weight or for GRAY (Gray ranks of the wrong weight are
- * skipped), else the C(n, w) ranks of the weight-w class in order.  Writes the
- * vectors whose bit is clear, in rank order; returns how many were clear. */
+ * the candidates in order (all 2^n vectors, or the C(n, w) weight-w vectors
+ * of the order when a weight is given; rank i is the i-th candidate).  Writes
+ * the vectors whose bit is clear, in rank order; returns how many were
+ * clear. */
 int64_t orc_scan(int n, int ord, int w, const uint32_t *bitmap, uint64_t rank0,
                  uint64_t count, uint32_t *out, int64_t cap) {
     if (!valid_args(n, ord, w)) return ORC_EINVAL;
     int64_t found = 0;
     uint64_t r = 0;
-    if (ord == ORC_GRAY || w < 0) {
-        /* walk the full order with no weight, then apply the filter */
-        orc_iter it; iter_init(&it, n, ord, -1);
-        uint32_t x;
-        while (r < rank0 + count && iter_next(&it, &x)) {
-            if (r >= rank0 && (w < 0 || orc_popcount(x) == w) &&
-                !(bitmap[x >> 5] >> (x & 31) & 1)) {
-                if (found < cap) out[found] = x;
-                ++found;
-            }
-            ++r;
+    orc_iter it; iter_init(&it, n, ord, w);
+    uint32_t x;
+    while (r < rank0 + count && iter_next(&it, &x)) {
+        if (r >= rank0 && !(bitmap[x >> 5] >> (x & 31) & 1)) {
+            if (found < cap) out[found] = x;
+            ++found;
         }
-    } else {
-        orc_iter it; iter_init(&it, n, ord, w);
-        uint32_t x;
-        while (r < rank0 + count && iter_next(&it, &x)) {
-            if (r >= rank0 && !(bitmap[x >> 5] >> (x & 31) & 1)) {
-                if (found < cap) out[found] = x;
-                ++found;
-            }
-            ++r;
-        }
+        ++r;
     }
     return found;
 }
@@ -651,4 +638,22 @@ int orc64_verify(int n, int d, int ord, int w, const uint64_t *L, int64_t len) {
     free(cand);
     if (rc) return rc;
     return i == len ? 0 : 1;
+}
+
+/* ---- Cartesian product of two codes (Section 5, "Recursion in Self
+ * orthogonal codes") ------------------------------------------------------- */
+/* Every codeword of A followed by every codeword of B: out[i * nb + j] =
+ * (A[i] << len_b) | B[j], A's words outermost.  Returns na * nb, or
+ * ORC_EINVAL when the words would not fit 64 bits. */
+int64_t orc64_product(const uint64_t *A, int64_t na, const uint64_t *B, int64_t nb, int len_a,
+                      int len_b, uint64_t *out, int64_t cap) {
+    if (len_a < 0 || len_b < 0 || len_a + len_b > 64 || len_a + len_b < 1) return ORC_EINVAL;
+    int64_t k = 0;
+    for (int64_t i = 0; i < na; ++i)
+        for (int64_t j = 0; j < nb; ++j) {
+            uint64_t hi = (len_b == 64) ? 0 : (A[i] << len_b);
+            if (k < cap) out[k] = hi | B[j];
+            ++k;
+        }
+    return k;
 }

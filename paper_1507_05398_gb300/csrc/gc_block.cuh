@@ -2,7 +2,8 @@
 // compaction, the candidate-vs-codeword distance test (warp-level scan and
 // the CTA-wide 2-D tiling of it), and the in-order resolver.  Functions
 // documented as CTA-wide are called by every thread of a CTA of kBlock
-// threads (they contain __syncthreads).
+// threads (they contain __syncthreads).  Every primitive takes vectors of
+// either width: W = uint32_t (n <= 32) or uint64_t (n <= 64).
 #pragma once
 #include <cstdint>
 
@@ -27,9 +28,9 @@ struct BlockScratch {
 // ------------------------------------------------------------ compaction
 // CTA-wide.  Appends the calling threads' (keep, vx, vo) items, in thread
 // order, to x[base..) and off[base..).  Returns the new base (uniform).
-__device__ __forceinline__ uint32_t block_append(BlockScratch& bs, bool keep, uint32_t vx,
-                                                 uint32_t vo, uint32_t* x, uint32_t* off,
-                                                 uint32_t base) {
+template <typename W>
+__device__ __forceinline__ uint32_t block_append(BlockScratch& bs, bool keep, W vx, uint32_t vo,
+                                                 W* x, uint32_t* off, uint32_t base) {
     const int lane = lane_id(), warp = warp_id();
     const unsigned bal = __ballot_sync(kFull, keep);
     const uint32_t wpre = __popc(bal & ((1u << lane) - 1u));
@@ -59,13 +60,15 @@ __device__ __forceinline__ uint32_t block_append(BlockScratch& bs, bool keep, ui
 
 // CTA-wide.  Keeps the entries of x/off[0..n) whose dead flag is 0, in
 // order, in place.
-__device__ __forceinline__ uint32_t block_compact(BlockScratch& bs, uint32_t* x, uint32_t* off,
+template <typename W>
+__device__ __forceinline__ uint32_t block_compact(BlockScratch& bs, W* x, uint32_t* off,
                                                   const uint8_t* dead, uint32_t n) {
     uint32_t base = 0;
     for (uint32_t t0 = 0; t0 < n; t0 += kBlock) {
         const uint32_t i = t0 + threadIdx.x;
         const bool keep = i < n && !dead[i];
-        const uint32_t vx = keep ? x[i] : 0u, vo = (keep && off) ? off[i] : 0u;
+        const W vx = keep ? x[i] : W(0);
+        const uint32_t vo = (keep && off) ? off[i] : 0u;
         // every read of this tile happens before block_append's first barrier,
         // and an item never moves to a higher index, so in-place is safe
         base = block_append(bs, keep, vx, vo, x, off, base);
@@ -81,8 +84,8 @@ __device__ __forceinline__ uint32_t block_compact(BlockScratch& bs, uint32_t* x,
 // When shared_dead is given it is re-read every 32 codewords so that other
 // warps working on the same candidate can end this scan early.  Adds this
 // lane's tests to nt.
-template <bool kGlobalSrc, bool kOrth = false>
-__device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const uint32_t* src,
+template <bool kGlobalSrc, bool kOrth = false, typename W>
+__device__ __forceinline__ bool warp_scan_desc(W x, bool is_dead, const W* src,
                                                uint32_t lo, uint32_t hi, int d,
                                                const volatile uint8_t* shared_dead, bool have,
                                                uint64_t& nt) {
@@ -92,17 +95,27 @@ __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const u
         if (__all_sync(kFull, is_dead)) break;
         uint32_t jlo;
         if (!kGlobalSrc && (j & 31u) == 0u && j - lo >= 32u) {
-            // 32 codewords as 8 broadcast 16-byte shared-memory loads
+            // 32 codewords as 8 (narrow) or 16 (wide) broadcast 16-byte
+            // shared-memory loads
             jlo = j - 32u;
             const uint4* p4 = reinterpret_cast<const uint4*>(src + jlo);
+            constexpr int kVecs = 32 * (int)sizeof(W) / 16;
 #pragma unroll
-            for (int q = 7; q >= 0; --q) {
+            for (int q = kVecs - 1; q >= 0; --q) {
                 const uint4 c = p4[q];
-                bool hit = (__popc(x ^ c.w) < d) | (__popc(x ^ c.z) < d) |
-                           (__popc(x ^ c.y) < d) | (__popc(x ^ c.x) < d);
-                if (kOrth)  // Section 4.4: also a conflict if not orthogonal
-                    hit |= ((__popc(x & c.w) | __popc(x & c.z) | __popc(x & c.y) |
-                             __popc(x & c.x)) & 1u) != 0u;
+                bool hit;
+                if constexpr (sizeof(W) == 4) {
+                    hit = (__popc(x ^ c.w) < d) | (__popc(x ^ c.z) < d) |
+                          (__popc(x ^ c.y) < d) | (__popc(x ^ c.x) < d);
+                    if (kOrth)  // Section 4.4: also a conflict if not orthogonal
+                        hit |= ((__popc(x & c.w) | __popc(x & c.z) | __popc(x & c.y) |
+                                 __popc(x & c.x)) & 1u) != 0u;
+                } else {
+                    const uint64_t c0 = ((uint64_t)c.y << 32) | c.x;
+                    const uint64_t c1 = ((uint64_t)c.w << 32) | c.z;
+                    hit = (__popcll(x ^ c1) < d) | (__popcll(x ^ c0) < d);
+                    if (kOrth) hit |= ((__popcll(x & c1) | __popcll(x & c0)) & 1) != 0;
+                }
                 is_dead |= hit;
             }
         } else {
@@ -110,9 +123,9 @@ __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const u
             jlo = (j & 31u) ? (j & ~31u) : j - 32u;
             if (jlo < lo || jlo > j) jlo = lo;
             for (uint32_t q = j; q > jlo; --q) {
-                const uint32_t c = kGlobalSrc ? ld_cg(src + q - 1) : src[q - 1];
-                is_dead |= (__popc(x ^ c) < d);
-                if (kOrth) is_dead |= (__popc(x & c) & 1) != 0;
+                const W c = kGlobalSrc ? ld_cg(src + q - 1) : src[q - 1];
+                is_dead |= (popc(x ^ c) < d);
+                if (kOrth) is_dead |= (popc(x & c) & 1) != 0;
             }
         }
         if (have) nt += j - jlo;
@@ -127,10 +140,9 @@ __device__ __forceinline__ bool warp_scan_desc(uint32_t x, bool is_dead, const u
 // the codeword range is split across warps as well (most recent slice to the
 // lowest warps), so a short list of hard candidates still keeps the whole CTA
 // busy.  Callers clear dead[] before and synchronise after.
-template <bool kGlobalSrc, bool kOrth = false>
-__device__ __forceinline__ void block_test(const uint32_t* xs, uint32_t na, uint8_t* dead,
-                                           const uint32_t* src, uint32_t lo, uint32_t hi, int d,
-                                           uint64_t& nt) {
+template <bool kGlobalSrc, bool kOrth = false, typename W>
+__device__ __forceinline__ void block_test(const W* xs, uint32_t na, uint8_t* dead, const W* src,
+                                           uint32_t lo, uint32_t hi, int d, uint64_t& nt) {
     if (na == 0 || hi <= lo) return;
     const int lane = lane_id(), warp = warp_id();
     const uint32_t ngroups = (na + 31) / 32;
@@ -144,7 +156,7 @@ __device__ __forceinline__ void block_test(const uint32_t* xs, uint32_t na, uint
         const uint32_t g = it % ngroups, s = it / ngroups;
         const uint32_t i = g * 32 + lane;
         const bool have = i < na;
-        const uint32_t x = have ? xs[i] : 0u;
+        const W x = have ? xs[i] : W(0);
         const bool was_dead = !have || dead[i];
         const uint32_t top = (uint64_t)s * per >= len ? lo : hi - s * per;
         const uint32_t bot = (top - lo > per) ? top - per : lo;
@@ -158,9 +170,9 @@ __device__ __forceinline__ void block_test(const uint32_t* xs, uint32_t na, uint
 
 // CTA-wide.  Tests x[0..na) against src[lo..hi) (block_test) and keeps the
 // candidates that clear it, in order, in place.  Returns how many are left.
-template <bool kGlobalSrc>
-__device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, uint32_t* x, uint32_t* off,
-                                                 uint8_t* dead, uint32_t na, const uint32_t* src,
+template <bool kGlobalSrc, typename W>
+__device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, W* x, uint32_t* off,
+                                                 uint8_t* dead, uint32_t na, const W* src,
                                                  uint32_t lo, uint32_t hi, int d, uint64_t& nt) {
     if (na == 0 || hi <= lo) return na;
     for (uint32_t i = threadIdx.x; i < na; i += kBlock) dead[i] = 0;
@@ -188,10 +200,10 @@ __device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, uint32_t* x, 
 // Returns the number accepted.
 // tim (optional, thread 0 only): cycles added to tim[0] matrix build,
 // tim[1] rounds, tim[2] append and kill step; tim[3] counts rounds.
-template <bool kOrth = false>
-__device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x, uint32_t* off,
+template <bool kOrth = false, typename W>
+__device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32_t* off,
                                                   uint8_t* dead, uint32_t n, int d,
-                                                  uint32_t* acc, uint32_t* acc_off,
+                                                  W* acc, uint32_t* acc_off,
                                                   uint32_t (*Mt)[kResolveBlock], uint64_t& nt,
                                                   unsigned long long* tim = nullptr,
                                                   uint32_t block = kResolveBlock) {
@@ -219,7 +231,7 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
     while (start < end) {
         const uint32_t P = min(block, end - start);
         const uint32_t nwords = (P + 31u) / 32u;
-        const uint32_t* bx = x + start;
+        const W* bx = x + start;
         // conflict matrix, strictly lower triangle, stored transposed
         // (Mt[word][row]) so both the build and the rounds read consecutive
         // shared-memory words across a warp: a warp owns a row, lane = column
@@ -228,22 +240,22 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
         // four rows per warp share each column load
         for (uint32_t i0 = warp * 4u; i0 < P; i0 += kWarps * 4u) {
             const uint32_t nr = min(4u, P - i0);
-            const uint32_t x0 = bx[i0];
-            const uint32_t x1 = nr > 1 ? bx[i0 + 1] : 0u;
-            const uint32_t x2 = nr > 2 ? bx[i0 + 2] : 0u;
-            const uint32_t x3 = nr > 3 ? bx[i0 + 3] : 0u;
+            const W x0 = bx[i0];
+            const W x1 = nr > 1 ? bx[i0 + 1] : W(0);
+            const W x2 = nr > 2 ? bx[i0 + 2] : W(0);
+            const W x3 = nr > 3 ? bx[i0 + 3] : W(0);
             const uint32_t last = (i0 + nr - 1) >> 5;  // word holding the last row's diagonal
             for (uint32_t wd = 0; wd <= last; ++wd) {
                 const uint32_t j = (wd << 5) + lane;
-                const uint32_t c = bx[j < P ? j : 0];
+                const W c = bx[j < P ? j : 0];
                 const unsigned b0 = __ballot_sync(
-                    kFull, j < i0 && ((__popc(x0 ^ c) < d) || (orth && (__popc(x0 & c) & 1))));
+                    kFull, j < i0 && ((popc(x0 ^ c) < d) || (orth && (popc(x0 & c) & 1))));
                 const unsigned b1 = __ballot_sync(
-                    kFull, j < i0 + 1 && ((__popc(x1 ^ c) < d) || (orth && (__popc(x1 & c) & 1))));
+                    kFull, j < i0 + 1 && ((popc(x1 ^ c) < d) || (orth && (popc(x1 & c) & 1))));
                 const unsigned b2 = __ballot_sync(
-                    kFull, j < i0 + 2 && ((__popc(x2 ^ c) < d) || (orth && (__popc(x2 & c) & 1))));
+                    kFull, j < i0 + 2 && ((popc(x2 ^ c) < d) || (orth && (popc(x2 & c) & 1))));
                 const unsigned b3 = __ballot_sync(
-                    kFull, j < i0 + 3 && ((__popc(x3 ^ c) < d) || (orth && (__popc(x3 & c) & 1))));
+                    kFull, j < i0 + 3 && ((popc(x3 ^ c) < d) || (orth && (popc(x3 & c) & 1))));
                 if (lane == 0) {
                     Mt[wd][i0] = b0;
                     if (nr > 1) Mt[wd][i0 + 1] = b1;
@@ -310,13 +322,13 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, uint32_t* x,
         for (uint32_t t0 = 0; t0 < P; t0 += kBlock) {
             const uint32_t i = t0 + threadIdx.x;
             const bool keep = i < P && ((bs.accb[i >> 5] >> (i & 31)) & 1u);
-            nacc = block_append(bs, keep, keep ? bx[i] : 0u,
+            nacc = block_append(bs, keep, keep ? bx[i] : W(0),
                                 (keep && acc_off) ? off[start + i] : 0u, acc, acc_off, nacc);
         }
         // the rest of the list against the block's accepts
         const uint32_t rest = end - (start + P);
         if (rest > 0 && nacc > nacc0) {
-            uint32_t* rx = x + start + P;
+            W* rx = x + start + P;
             uint32_t* ro = off ? off + start + P : nullptr;
             for (uint32_t i = threadIdx.x; i < rest; i += kBlock) dead[i] = 0;
             __syncthreads();

@@ -21,15 +21,15 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+// C(n, k) for 0 <= n <= 64 (exact: the largest, C(64, 32), is below 2^61).
 uint64_t binom64(int n, int k) {
-    if (k < 0 || n < 0 || k > n) return 0;
-    uint64_t r = 1;
-    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
-    return r;
+    if (k < 0 || n < 0 || k > n || n > kMaxNWide) return 0;
+    static const Binom64Table table = make_binom64();
+    return table.c[n][k];
 }
 
-static uint64_t ball_volume(int n, int r) {
-    uint64_t v = 0;
+static unsigned __int128 ball_volume(int n, int r) {
+    unsigned __int128 v = 0;
     for (int k = 0; k <= r && k <= n; ++k) v += binom64(n, k);
     return v;
 }
@@ -66,8 +66,8 @@ static bool invert_basis(int n, const uint32_t* basis, uint32_t* inv) {
     return true;
 }
 
-bool make_problem(const gc_problem& q, HostProblem* p, std::string* why) {
-    return make_problem(q.n, q.d, q.ordering, q.weight, p, why, q.constraint, q.basis);
+bool make_problem(const gc_problem& q, HostProblem* p, std::string* why, int max_n) {
+    return make_problem(q.n, q.d, q.ordering, q.weight, p, why, q.constraint, q.basis, max_n);
 }
 
 Order order_of(const HostProblem& p, bool filter, bool even) {
@@ -79,7 +79,7 @@ Order order_of(const HostProblem& p, bool filter, bool even) {
     o.even = even;
     o.N = p.N;
     uint64_t c = 0;
-    for (int k = 0; k <= kMaxN + 1; ++k) {
+    for (int k = 0; k <= kMaxNWide + 1; ++k) {
         o.cum[k] = c;
         if (k <= p.n) c += binom64(p.n, k);
     }
@@ -91,10 +91,22 @@ Order order_of(const HostProblem& p, bool filter, bool even) {
 }
 
 bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why, int constraint,
-                  const uint32_t* basis) {
-    if (n < 1 || n > 32) { *why = "n must be in [1, 32]"; return false; }
+                  const uint32_t* basis, int max_n) {
+    if (n < 1 || n > max_n) {
+        *why = max_n > kMaxN ? "n must be in [1, 64]"
+                             : "n must be in [1, 32] (up to 64 through the *64 entry points)";
+        return false;
+    }
     if (d < 0) { *why = "d must be >= 0"; return false; }
     if (ord < GC_ORDER_LEX || ord > GC_ORDER_BASIS) { *why = "unknown ordering"; return false; }
+    if (n > kMaxN && ord == GC_ORDER_BASIS) {
+        *why = "B-orderings take n <= 32";
+        return false;
+    }
+    if (n == kMaxNWide && w < 0) {
+        *why = "n = 64 needs a weight (2^64 ranks do not fit a count)";
+        return false;
+    }
     for (int j = 0; j < 32; ++j) p->basis[j] = p->inv[j] = 0;
     if (ord == GC_ORDER_BASIS) {
         if (!basis) { *why = "GC_ORDER_BASIS needs a basis"; return false; }
@@ -114,13 +126,14 @@ bool make_problem(int n, int d, int ord, int w, HostProblem* p, std::string* why
     p->d = d;
     p->ord = ord;
     p->w = w;
-    p->filter = (w >= 0 && (ord == GC_ORDER_GRAY || ord == GC_ORDER_BASIS));
-    p->N = (w < 0 || ord == GC_ORDER_GRAY || ord == GC_ORDER_BASIS) ? (1ull << n) : binom64(n, w);
+    p->filter = (w >= 0 && ord == GC_ORDER_BASIS);
+    p->N = (w < 0 || ord == GC_ORDER_BASIS) ? (1ull << n) : binom64(n, w);
     p->valid = (w < 0) ? (1ull << n) : binom64(n, w);
     // sphere packing: radius floor((d-1)/2) balls around codewords are disjoint
     const int t = d >= 1 ? (d - 1) / 2 : 0;
-    const uint64_t hb = (1ull << n) / ball_volume(n, t);
-    p->bound = std::max<uint64_t>(1, std::min<uint64_t>(p->valid, hb));
+    const unsigned __int128 hb = ((unsigned __int128)1 << n) / ball_volume(n, t);
+    p->bound = std::max<uint64_t>(
+        1, hb < (unsigned __int128)p->valid ? (uint64_t)hb : p->valid);
     if (d <= 1) p->bound = p->valid;
     if (p->orth) p->bound = std::min<uint64_t>(p->bound, 1ull << (n / 2));
     return true;
@@ -139,7 +152,8 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
     pl->window_min = 256;
     pl->window_max = 0;
     pl->survivor_target = 256;
-    if (p.d <= 1 || p.orth) {  // orthogonality cannot be marked in a bitmap
+    // orthogonality cannot be marked in a bitmap; n > 32 has no bitmap form
+    if (p.d <= 1 || p.orth || p.n > kMaxN) {
         pl->strategy = GC_STRATEGY_DISTANCE;
         return;
     }
@@ -184,6 +198,18 @@ static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* o
     return out->strategy == GC_STRATEGY_DISTANCE || out->strategy == GC_STRATEGY_BITMAP;
 }
 
+// The plan of a wide sweep: the distance strategy (the bitmap has no wide
+// form); an explicit bitmap request fails.
+static bool resolve_plan_wide(const HostProblem& p, const gc_plan_t* in, gc_plan_t* out) {
+    if (!resolve_plan(p, in, out)) return false;
+    if (out->strategy == GC_STRATEGY_BITMAP) {
+        if (in && in->strategy == GC_STRATEGY_BITMAP) return false;
+        out->strategy = GC_STRATEGY_DISTANCE;
+        out->survivor_target = (in && in->survivor_target) ? in->survivor_target : 256;
+    }
+    return true;
+}
+
 static bool is_device_ptr(const void* ptr) {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
@@ -207,17 +233,18 @@ __global__ void all_accepted_stats(gc_stats* st, uint64_t N, int strategy) {
     for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
 }
 
-static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint32_t* d_out,
+// wide: run the uint64-word kernel (n <= 64; d_out holds uint64 words).
+static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, void* d_out,
                                uint64_t capacity, gc_stats* d_stats, void* ws, size_t ws_bytes,
-                               cudaStream_t s) {
-    if (p.d <= 1 && !p.filter && !p.orth) {
-        int rc = launch_unrank(p, 0, std::min(capacity, p.N), d_out, s);
+                               cudaStream_t s, bool wide = false) {
+    if (p.d <= 1 && !p.filter && !p.orth && !wide) {
+        int rc = launch_unrank(p, 0, std::min(capacity, p.N), static_cast<uint32_t*>(d_out), s);
         if (rc) return rc;
         all_accepted_stats<<<1, 1, 0, s>>>(d_stats, p.N, plan.strategy);
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? GC_OK : fail(GC_ERR_CUDA, cudaGetErrorString(e));
     }
-    BatchJob job{p, plan, d_out, capacity, d_stats};
+    BatchJob job{p, plan, d_out, capacity, d_stats, wide};
     BatchLayout L;
     std::string why;
     if (!batch_layout(&job, 1, 1, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
@@ -228,9 +255,10 @@ static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, uint
     return GC_OK;
 }
 
-static size_t single_workspace(const HostProblem& p, const gc_plan_t& pl, std::string* why) {
-    if (p.d <= 1 && !p.filter && !p.orth) return 256;
-    BatchJob job{p, pl, nullptr, 0, nullptr};
+static size_t single_workspace(const HostProblem& p, const gc_plan_t& pl, std::string* why,
+                               bool wide = false) {
+    if (p.d <= 1 && !p.filter && !p.orth && !wide) return 256;
+    BatchJob job{p, pl, nullptr, 0, nullptr, wide};
     BatchLayout L;
     if (!batch_layout(&job, 1, 1, &L, why)) return 0;
     return L.total;
@@ -285,15 +313,18 @@ const char* gc_last_error(void) { return g_last_error.c_str(); }
 uint64_t gc_candidate_count(int n, int w, int ordering) {
     HostProblem p;
     std::string why;
-    if (ordering == GC_ORDER_BASIS) ordering = GC_ORDER_GRAY;  // same rank space
-    if (!make_problem(n, 2, ordering, w, &p, &why)) return 0;
+    if (ordering == GC_ORDER_BASIS)  // 2^n ranks whatever the basis
+        return (n >= 1 && n <= kMaxN && w >= -1 && w <= n) ? (1ull << n) : 0;
+    if (!make_problem(n, 2, ordering, w, &p, &why, GC_CONSTRAINT_NONE, nullptr, kMaxNWide))
+        return 0;
     return p.N;
 }
 
 uint64_t gc_capacity_bound(int n, int d, int w) {
     HostProblem p;
     std::string why;
-    if (!make_problem(n, d, GC_ORDER_LEX, w, &p, &why)) return 0;
+    if (!make_problem(n, d, GC_ORDER_LEX, w, &p, &why, GC_CONSTRAINT_NONE, nullptr, kMaxNWide))
+        return 0;
     return p.bound;
 }
 
@@ -329,33 +360,37 @@ int gc_generate_async(const gc_problem* prob, const gc_plan_t* plan, uint32_t* d
                                (cudaStream_t)stream);
 }
 
-int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inout_count) {
-    if (!inout_count || (!out && *inout_count > 0)) return fail(GC_ERR_INVALID, "null argument");
-    HostProblem p;
+}  // extern "C"
+
+// The synchronous call: host or device output of `wbytes`-byte words.
+static int generate_sync(const HostProblem& p, void* out, uint64_t* inout_count, bool wide) {
     std::string why;
-    if (!make_problem(n, d, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
     gc_plan_t pl;
-    resolve_plan(p, nullptr, &pl);
+    if (wide)
+        resolve_plan_wide(p, nullptr, &pl);
+    else
+        resolve_plan(p, nullptr, &pl);
+    const size_t wbytes = wide ? 8 : 4;
     const uint64_t cap = *inout_count;
     const bool dev_out = cap > 0 && is_device_ptr(out);
-    const size_t ws_bytes = single_workspace(p, pl, &why);
+    const size_t ws_bytes = single_workspace(p, pl, &why, wide);
     if (ws_bytes == 0) return fail(GC_ERR_UNSUPPORTED, why);
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
         return fail(GC_ERR_CUDA, "stream create");
     void* ws = nullptr;
     gc_stats* d_stats = nullptr;
-    uint32_t* d_buf = nullptr;
+    void* d_buf = nullptr;
     const uint64_t dcap = dev_out ? 0 : std::min<uint64_t>(cap, p.bound);
     int rc = GC_OK;
     cudaError_t e;
     if ((e = cudaMallocAsync(&ws, ws_bytes, s)) != cudaSuccess ||
         (e = cudaMallocAsync((void**)&d_stats, sizeof(gc_stats), s)) != cudaSuccess ||
-        (dcap && (e = cudaMallocAsync((void**)&d_buf, dcap * 4, s)) != cudaSuccess)) {
+        (dcap && (e = cudaMallocAsync(&d_buf, dcap * wbytes, s)) != cudaSuccess)) {
         rc = fail(e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA, cudaGetErrorString(e));
     }
     if (!rc) rc = generate_async_impl(p, pl, dev_out ? out : d_buf, dev_out ? cap : dcap, d_stats,
-                                      ws, ws_bytes, s);
+                                      ws, ws_bytes, s, wide);
     gc_stats st{};
     if (!rc) {
         if ((e = cudaMemcpyAsync(&st, d_stats, sizeof st, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -365,7 +400,7 @@ int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inou
     if (!rc && st.status != 0) rc = fail(st.status, "device-side error in the sweep");
     if (!rc && !dev_out && dcap) {
         const uint64_t ncopy = std::min<uint64_t>(st.codewords, dcap);
-        if ((e = cudaMemcpy(out, d_buf, ncopy * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        if ((e = cudaMemcpy(out, d_buf, ncopy * wbytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
             rc = fail(GC_ERR_CUDA, cudaGetErrorString(e));
     }
     if (d_buf) cudaFreeAsync(d_buf, s);
@@ -377,6 +412,50 @@ int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inou
     *inout_count = st.codewords;
     if (st.codewords > cap) return fail(GC_ERR_CAPACITY, "output capacity too small");
     return GC_OK;
+}
+
+extern "C" {
+
+int gc_generate(int n, int d, int ordering, int w, uint32_t* out, uint64_t* inout_count) {
+    if (!inout_count || (!out && *inout_count > 0)) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, d, ordering, w, &p, &why)) return fail(GC_ERR_INVALID, why);
+    return generate_sync(p, out, inout_count, false);
+}
+
+// ---- wide vectors (uint64 words, n <= 64) ----
+size_t gc_workspace_size64(const gc_problem* prob, const gc_plan_t* plan) {
+    if (!prob) return 0;
+    HostProblem p;
+    std::string why;
+    if (!make_problem(*prob, &p, &why, kMaxNWide)) return 0;
+    gc_plan_t pl;
+    if (!resolve_plan_wide(p, plan, &pl)) return 0;
+    return single_workspace(p, pl, &why, true);
+}
+
+int gc_generate64_async(const gc_problem* prob, const gc_plan_t* plan, uint64_t* d_out,
+                        uint64_t capacity, gc_stats* d_stats, void* workspace,
+                        size_t workspace_bytes, void* stream) {
+    if (!prob || !d_stats || (!d_out && capacity > 0)) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(*prob, &p, &why, kMaxNWide)) return fail(GC_ERR_INVALID, why);
+    gc_plan_t pl;
+    if (!resolve_plan_wide(p, plan, &pl))
+        return fail(GC_ERR_UNSUPPORTED, "the wide sweep runs the distance strategy only");
+    return generate_async_impl(p, pl, d_out, capacity, d_stats, workspace, workspace_bytes,
+                               (cudaStream_t)stream, true);
+}
+
+int gc_generate64(int n, int d, int ordering, int w, uint64_t* out, uint64_t* inout_count) {
+    if (!inout_count || (!out && *inout_count > 0)) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(n, d, ordering, w, &p, &why, GC_CONSTRAINT_NONE, nullptr, kMaxNWide))
+        return fail(GC_ERR_INVALID, why);
+    return generate_sync(p, out, inout_count, true);
 }
 
 size_t gc_batch_workspace_size(const gc_job* jobs, int njobs, int ngroups) {

@@ -1,11 +1,14 @@
 // gc_device.cuh -- device-side building blocks of the greedy sweep (sm_103a).
 //
-// Vectors are the low n bits of a uint32 with coordinate 1 as the most
-// significant of them.  The four orders of Section 4.2 are turned into
-// closed-form rank <-> vector maps so that any window of ranks can be
-// generated in parallel without materialising the order:
+// Vectors are the low n bits of a uint32 (n <= 32) or, in the wide forms, of
+// a uint64 (n <= 64), with coordinate 1 as the most significant of them.  The
+// four orders of Section 4.2 are turned into closed-form rank <-> vector maps
+// so that any window of ranks can be generated in parallel without
+// materialising the order:
 //   LEX      rank r is the vector r.
-//   GRAY     rank r is r ^ (r >> 1); the inverse is a prefix XOR.
+//   GRAY     rank r is r ^ (r >> 1); the inverse is a prefix XOR.  With a
+//            weight w the ranks are those of the weight-w vectors only, in
+//            the same order (gray_weight_unrank).
 //   GRLEX    weight classes in ascending weight; inside class k the i-th
 //            vector is the i-th smallest n-bit integer of weight k, found with
 //            the combinatorial number system.
@@ -18,7 +21,8 @@
 
 namespace gc {
 
-constexpr int kMaxN = 32;
+constexpr int kMaxN = 32;       // narrow vectors (uint32 words)
+constexpr int kMaxNWide = 64;   // wide vectors (uint64 words)
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------- binomials
@@ -68,6 +72,89 @@ __device__ __forceinline__ uint32_t comb_rank(const uint32_t (*C)[kMaxN + 1], ui
 
 __device__ __forceinline__ uint32_t reverse_n(uint32_t v, int n) { return __brev(v) >> (32 - n); }
 
+// i-th (0-based) n-bit vector of weight w in Gray order.  The vector of Gray
+// rank r is r ^ (r >> 1), whose weight is the number of places where r
+// changes between neighbouring bits, reading down from a 0 above bit n-1.  The
+// rank is built from the top bit down, 0 before 1: with t changes so far and
+// the bit above equal to `prev`, putting b at bit p leaves the p bits below it,
+// whose p neighbour pairs must hold the w - t - [b != prev] remaining changes:
+// C(p, w - t - [b != prev]) ways.
+__device__ __forceinline__ uint32_t gray_weight_unrank(const uint32_t (*C)[kMaxN + 1], int n,
+                                                       int w, uint32_t i) {
+    uint32_t r = 0;
+    int prev = 0, t = 0;
+    for (int p = n - 1; p >= 0; --p) {
+        const int t0 = t + (prev != 0);
+        const uint32_t c0 = (w - t0 >= 0) ? C[p][w - t0] : 0u;
+        if (i < c0) {
+            t = t0;
+            prev = 0;
+        } else {
+            i -= c0;
+            r |= 1u << p;
+            t += (prev != 1);
+            prev = 1;
+        }
+    }
+    return r ^ (r >> 1);
+}
+
+// Wide forms: C(p, k) for p, k <= 64 (Pascal's rule; C(64, 32) < 2^61), read
+// through the read-only cache from a table initialised at compile time.
+struct Binom64Table {
+    uint64_t c[kMaxNWide + 1][kMaxNWide + 1];
+};
+constexpr Binom64Table make_binom64() {
+    Binom64Table t{};
+    for (int p = 0; p <= kMaxNWide; ++p)
+        for (int k = 0; k <= kMaxNWide; ++k)
+            t.c[p][k] = (k == 0) ? 1ull : (p == 0 ? 0ull : t.c[p - 1][k - 1] + t.c[p - 1][k]);
+    return t;
+}
+
+__device__ __forceinline__ uint64_t comb_unrank64(const Binom64Table& C, int n, int k,
+                                                  uint64_t i) {
+    uint64_t x = 0;
+    for (int p = n - 1; p >= 0 && k > 0; --p) {
+        const uint64_t c = __ldg(&C.c[p][k]);
+        if (i >= c) {
+            x |= 1ull << p;
+            i -= c;
+            --k;
+        }
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint64_t reverse_n64(uint64_t v, int n) {
+    return __brevll(v) >> (64 - n);
+}
+
+// Wide form of gray_weight_unrank.
+__device__ __forceinline__ uint64_t gray_weight_unrank64(const Binom64Table& C, int n, int w,
+                                                         uint64_t i) {
+    uint64_t r = 0;
+    int prev = 0, t = 0;
+    for (int p = n - 1; p >= 0; --p) {
+        const int t0 = t + (prev != 0);
+        const uint64_t c0 = (w - t0 >= 0) ? __ldg(&C.c[p][w - t0]) : 0ull;
+        if (i < c0) {
+            t = t0;
+            prev = 0;
+        } else {
+            i -= c0;
+            r |= 1ull << p;
+            t += (prev != 1);
+            prev = 1;
+        }
+    }
+    return r ^ (r >> 1);
+}
+
+// Population counts of either word width.
+__device__ __forceinline__ int popc(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ int popc(uint64_t v) { return __popcll(v); }
+
 __device__ __forceinline__ uint32_t gray_inverse(uint32_t g) {
     g ^= g >> 1;
     g ^= g >> 2;
@@ -85,27 +172,26 @@ struct Order {
     int n;
     int ord;
     int w;          // -1 = every weight
-    bool filter;    // ranks whose vector has the wrong weight are skipped
+    bool filter;    // BASIS with a weight: ranks of the wrong weight are skipped
     bool even;      // only even-weight vectors are candidates (self-orthogonal)
     uint64_t N;     // rank-space size
     // graded orders without a weight: cum[k] = number of vectors of weight < k
-    uint64_t cum[kMaxN + 2];
+    uint64_t cum[kMaxNWide + 2];
     // B-ordering (Section 4.3): basis[j] = b_{j+1}; inv[j] = row j of the
     // inverse, so bit j of the rank of v is the parity of (v AND inv[j])
     uint32_t basis[kMaxN];
     uint32_t inv[kMaxN];
 };
 
-// Vector of rank r (r < N).  Returns false when the rank is skipped: a Gray
-// rank of the wrong weight, or an odd-weight vector when only even ones are
-// candidates.
+// Vector of rank r (r < N).  Returns false when the rank is skipped: a
+// B-ordering rank of the wrong weight, or an odd-weight vector when only even
+// ones are candidates.
 __device__ __forceinline__ bool unrank(const Order& o, const uint32_t (*C)[kMaxN + 1], uint64_t r,
                                        uint32_t& x) {
     const int n = o.n;
     bool ok = true;
     if (o.ord == kGray) {
-        x = (uint32_t)(r ^ (r >> 1));
-        ok = !o.filter || __popc(x) == o.w;
+        x = o.w >= 0 ? gray_weight_unrank(C, n, o.w, (uint32_t)r) : (uint32_t)(r ^ (r >> 1));
     } else if (o.ord == kBasis) {
         x = 0;
         for (uint64_t b = r; b; b &= b - 1) x ^= o.basis[__ffsll((long long)b) - 1];
@@ -132,6 +218,38 @@ __device__ __forceinline__ bool unrank(const Order& o, const uint32_t (*C)[kMaxN
         }
     }
     if (o.even && (__popc(x) & 1)) ok = false;
+    return ok;
+}
+
+// Wide form of unrank for n <= 64 (LEX, GRAY, GRLEX, GREVLEX; B-orderings
+// are narrow only).
+__device__ __forceinline__ bool unrank_wide(const Order& o, const Binom64Table& C, uint64_t r,
+                                            uint64_t& x) {
+    const int n = o.n;
+    bool ok = true;
+    if (o.ord == kGray) {
+        x = o.w >= 0 ? gray_weight_unrank64(C, n, o.w, r) : (r ^ (r >> 1));
+    } else if (o.ord == kLex && o.w < 0) {
+        x = r;
+    } else {
+        int k;
+        uint64_t i;
+        if (o.w >= 0) {
+            k = o.w;
+            i = r;
+        } else {
+            k = 0;
+            while (k < n && o.cum[k + 1] <= r) ++k;
+            i = r - o.cum[k];
+        }
+        if (o.ord == kGrevlex) {
+            const uint64_t m = __ldg(&C.c[n][k]) - 1 - i;
+            x = reverse_n64(comb_unrank64(C, n, k, m), n);
+        } else {
+            x = comb_unrank64(C, n, k, i);
+        }
+    }
+    if (o.even && (__popcll(x) & 1)) ok = false;
     return ok;
 }
 
@@ -178,6 +296,9 @@ __device__ __forceinline__ unsigned atom_add_acqrel_gpu(unsigned* p, unsigned v)
 // Loads of data other CTAs wrote during this kernel: L2 only (L1 is not
 // coherent across SMs).
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ld_cg(const uint64_t* p) {
+    return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
 
 // ---------------------------------------------------------------- warp utils
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

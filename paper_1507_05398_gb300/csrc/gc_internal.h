@@ -13,7 +13,8 @@
 
 namespace gc {
 
-// Fully checked problem description shared by the launchers.
+// Fully checked problem description shared by the launchers.  n <= 32, or
+// n <= 64 for the wide entry points (uint64 words).
 struct HostProblem {
     int n, d, ord, w;
     bool orth;         // self-orthogonal constraint (Section 4.4)
@@ -27,9 +28,10 @@ struct HostProblem {
 
 uint64_t binom64(int n, int k);
 bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why,
-                  int constraint = GC_CONSTRAINT_NONE, const uint32_t* basis = nullptr);
+                  int constraint = GC_CONSTRAINT_NONE, const uint32_t* basis = nullptr,
+                  int max_n = kMaxN);
 // make_problem from the ABI struct
-bool make_problem(const gc_problem& q, HostProblem* out, std::string* why);
+bool make_problem(const gc_problem& q, HostProblem* out, std::string* why, int max_n = kMaxN);
 // Fills an Order for the device from a checked problem.
 Order order_of(const HostProblem& p, bool filter, bool even);
 // Strategy and launch shape for a problem (gc_plan).
@@ -49,7 +51,7 @@ struct JobDesc {
     Order ord;
     int d;
     int strategy;          // 1 distance, 2 bitmap
-    uint32_t* out;
+    void* out;             // uint32 words (narrow kernel) or uint64 words (wide)
     uint64_t cap;
     gc_stats* stats;
     const uint32_t* hball;
@@ -88,15 +90,17 @@ int launch_server(ServeLayout& L, void* ws, JobDesc* ring, unsigned* tail, unsig
 struct BatchJob {
     HostProblem p;
     gc_plan_t plan;     // strategy is DISTANCE or BITMAP here
-    uint32_t* d_out;
+    void* d_out;        // uint32 words, or uint64 words for a wide job
     uint64_t capacity;
     gc_stats* d_stats;
+    bool wide = false;  // run on the wide kernel (uint64 words, n <= 64)
 };
 
 // Where everything of a batched sweep lives: CTA groups, their jobs, and
 // the workspace offsets of the descriptors and scratch.
 struct BatchLayout {
     int grid = 0, ngroups = 0;
+    bool wide = false;          // the uint64-word kernel
     uint32_t cache_words = 0;   // shared-memory code cache (distance jobs)
     size_t smem_bytes = 0;
     std::vector<int> first_cta, ncta, job_begin, job_end, job_order;

@@ -262,4 +262,51 @@ int launch_bitmap_scan(const HostProblem& p, const uint32_t* d_bitmap, uint64_t 
     return check_launch("scan write");
 }
 
+// ---------------------------------------------------------------- product
+// Cartesian product of two codes (Section 5): out[i * nb + j] =
+// (a[i] << len_b) | b[j].  Grid-stride over the na * nb outputs.
+template <typename W>
+__global__ void product_kernel(const W* a, uint64_t na, const W* b, uint64_t nb, int len_b,
+                               W* out) {
+    const uint64_t total = na * nb;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = q / nb, j = q - i * nb;
+        out[q] = (W)((a[i] << len_b) | b[j]);
+    }
+}
+
+template <typename W>
+int launch_product(const W* d_a, uint64_t na, int len_a, const W* d_b, uint64_t nb, int len_b,
+                   W* d_out, uint64_t capacity, cudaStream_t s) {
+    const int bits = (int)(8 * sizeof(W));
+    if (len_a < 1 || len_b < 1 || len_a + len_b > bits)
+        return fail(GC_ERR_INVALID, "product: need 1 <= len_a, len_b and len_a + len_b <= " +
+                                        std::to_string(bits));
+    if ((na && !d_a) || (nb && !d_b)) return fail(GC_ERR_INVALID, "null pointer");
+    if (na && nb > UINT64_MAX / na) return fail(GC_ERR_INVALID, "product too large");
+    const uint64_t total = na * nb;
+    if (total > capacity) return fail(GC_ERR_CAPACITY, "product: output capacity too small");
+    if (total == 0) return GC_OK;
+    if (!d_out) return fail(GC_ERR_INVALID, "null pointer");
+    product_kernel<W><<<grid_for(total, 256 * 8), 256, 0, s>>>(d_a, na, d_b, nb, len_b, d_out);
+    return check_launch("product");
+}
+
 }  // namespace gc
+
+using namespace gc;
+
+extern "C" int gc_product(const uint32_t* d_a, uint64_t na, int len_a, const uint32_t* d_b,
+                          uint64_t nb, int len_b, uint32_t* d_out, uint64_t capacity,
+                          void* stream) {
+    return launch_product<uint32_t>(d_a, na, len_a, d_b, nb, len_b, d_out, capacity,
+                                    (cudaStream_t)stream);
+}
+
+extern "C" int gc_product64(const uint64_t* d_a, uint64_t na, int len_a, const uint64_t* d_b,
+                            uint64_t nb, int len_b, uint64_t* d_out, uint64_t capacity,
+                            void* stream) {
+    return launch_product<uint64_t>(d_a, na, len_a, d_b, nb, len_b, d_out, capacity,
+                                    (cudaStream_t)stream);
+}

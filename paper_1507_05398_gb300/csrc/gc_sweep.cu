@@ -27,6 +27,8 @@
 //     Every CTA keeps its own copy of the accepts, so no second wait is needed.
 // The window size adapts so that about `target` candidates survive step 1; if
 // more than kSurvCap survive, the window is cut after the kSurvCap-th one.
+// The kernel is instantiated for narrow vectors (uint32 words, n <= 32, both
+// strategies) and wide ones (uint64 words, n <= 64, distance strategy only).
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -49,9 +51,9 @@ struct GroupDesc {
     int first_cta, ncta;
     int job_begin, job_end;       // range of job_order
     unsigned long long* flags;    // [2][ncta]: (sequence << 32) | survivor count
-    uint32_t* seg_x;              // [2][ncta][kChunk]
+    void* seg_x;                  // [2][ncta][kChunk] vectors (the kernel's word type)
     uint32_t* seg_off;            // [2][ncta][kChunk]
-    uint32_t* store;              // distance jobs: code beyond the shared cache
+    void* store;                  // distance jobs: code beyond the shared cache
     uint64_t store_words;
     uint32_t* bitmap;             // bitmap jobs: 2^n bits, vector-indexed
 };
@@ -109,15 +111,16 @@ __device__ uint32_t serve_claim(const ServeQueue& q) {
     }
 }
 
+template <typename W>
 struct __align__(16) SweepSmem {
     uint32_t C[kMaxN + 1][kMaxN + 1];
     uint32_t pad0[3];
     uint32_t lowball[8][32];  // lowball[r][c]: bits y < 32 with popc(y ^ c) <= r
     uint32_t lowlight[8];     // lowlight[k]: bits y < 32 with popc(y) < k (k >= 6: all)
-    __align__(16) uint32_t list_x[kChunk];
+    __align__(16) W list_x[kChunk];
     __align__(16) uint32_t list_off[kChunk];
-    __align__(16) uint32_t accA[kSurvCap];
-    __align__(16) uint32_t accB[kSurvCap];
+    __align__(16) W accA[kSurvCap];
+    __align__(16) W accB[kSurvCap];
     __align__(16) uint32_t acc_off[kSurvCap];
     uint32_t M[kResolveWords][kResolveBlock];
     uint32_t pref[kMaxGroupCtas + 1];
@@ -172,7 +175,8 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // until every CTA of the group has published seq; then s.pref holds the
 // exclusive prefix of the counts and the total is returned.  Bounded: on
 // timeout (or when another CTA reported one) sets *ok = false.
-__device__ uint32_t group_exchange(SweepSmem& s, unsigned long long* flags, int lb, int gsize,
+template <typename W>
+__device__ uint32_t group_exchange(SweepSmem<W>& s, unsigned long long* flags, int lb, int gsize,
                                    uint32_t seq, uint32_t count, unsigned* err, long long timeout,
                                    bool* ok) {
     __threadfence();
@@ -209,10 +213,15 @@ __device__ uint32_t group_exchange(SweepSmem& s, unsigned long long* flags, int 
     return total;
 }
 
+// C(p, k) for p, k <= 64, for the wide kernel's graded orders.
+__device__ const Binom64Table g_binom64 = make_binom64();
+
+template <typename Word>
 __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant__ BatchArgs a) {
+    constexpr bool kWide = sizeof(Word) == 8;
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    SweepSmem& s = *reinterpret_cast<SweepSmem*>(smem_raw);
-    uint32_t* cache = reinterpret_cast<uint32_t*>(smem_raw + sizeof(SweepSmem));
+    SweepSmem<Word>& s = *reinterpret_cast<SweepSmem<Word>*>(smem_raw);
+    Word* cache = reinterpret_cast<Word*>(smem_raw + sizeof(SweepSmem<Word>));
     const int tid = threadIdx.x, lane = lane_id(), warp = warp_id();
 
     // which group this CTA belongs to
@@ -221,14 +230,17 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
         while (g + 1 < a.ngroups && a.groups[g + 1].first_cta <= (int)blockIdx.x) ++g;
         s.grp = a.groups[g];
     }
-    for (int q = tid; q < (kMaxN + 1) * (kMaxN + 1); q += kBlock) {
-        const int p = q / (kMaxN + 1), k = q % (kMaxN + 1);
-        uint64_t r = (k <= p) ? 1u : 0u;
-        for (int i = 1; i <= k && k <= p; ++i) r = r * (uint64_t)(p - k + i) / (uint64_t)i;
-        s.C[p][k] = (uint32_t)r;
-    }
+    if constexpr (!kWide)
+        for (int q = tid; q < (kMaxN + 1) * (kMaxN + 1); q += kBlock) {
+            const int p = q / (kMaxN + 1), k = q % (kMaxN + 1);
+            uint64_t r = (k <= p) ? 1u : 0u;
+            for (int i = 1; i <= k && k <= p; ++i) r = r * (uint64_t)(p - k + i) / (uint64_t)i;
+            s.C[p][k] = (uint32_t)r;
+        }
     __syncthreads();
     const GroupDesc& grp = s.grp;
+    Word* const seg_x = static_cast<Word*>(grp.seg_x);
+    Word* const store = static_cast<Word*>(grp.store);
     const int lb = (int)blockIdx.x - grp.first_cta;
     const int G = grp.ncta;
     const uint32_t(*C)[kMaxN + 1] = s.C;
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
         const Order& o = job.ord;
         const int d = job.d;
         const int n = o.n;
-        {
+        if (!kWide && job.strategy == kStratBitmap) {
             const int nl = n < 5 ? n : 5;
             for (int q = tid; q < 8 * 32; q += kBlock) {
                 const int r = q / 32, c = q % 32;
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             }
         }
         // job start: clear this CTA's share of the bitmap
-        if (job.strategy == kStratBitmap) {
+        if (!kWide && job.strategy == kStratBitmap) {
             const uint64_t words = ((1ull << n) + 31) / 32;
             const uint64_t per = (words + G - 1) / G;
             const uint64_t w0 = min((uint64_t)lb * per, words), w1 = min(w0 + per, words);
@@ -308,8 +320,8 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
 
         uint64_t R0 = 0, K = 0, Kprev = 0;
         uint32_t W = job.wmin;
-        uint32_t* cur = s.accA;
-        uint32_t* prev = s.accB;
+        Word* cur = s.accA;
+        Word* prev = s.accB;
         uint32_t nprev = 0;
         uint64_t my_tests = 0, my_marks = 0, dense = 0, resolve_tests = 0;
         uint64_t windows = 0, surv_total = 0;
@@ -332,7 +344,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             const uint64_t c1 = min(c0 + chunk, R0 + span);
 
             // bitmap strategy: this CTA's share of the previous window's marks
-            if (job.strategy == kStratBitmap && nprev > 0) {
+            if (!kWide && job.strategy == kStratBitmap && nprev > 0) {
                 const uint32_t hl = job.hball_len;
                 const uint64_t total = (uint64_t)nprev * hl;
                 const uint64_t per = (total + G - 1) / G;
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 uint32_t i = (uint32_t)(qs / hl), j = (uint32_t)(qs - (uint64_t)i * hl);
                 const uint32_t di = kBlock / hl, dj = kBlock - di * hl;
                 for (uint64_t q = qs; q < q1; q += kBlock) {
-                    const uint32_t c = prev[i];
+                    const uint32_t c = (uint32_t)prev[i];
                     const uint32_t e = __ldg(job.hball + j);
                     const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
                     uint32_t mask = s.lowball[e & 7u][c & 31u];
@@ -375,12 +387,16 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             uint32_t na = 0;
             for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
                 const uint64_t r = t0 + tid;
-                uint32_t x = 0;
+                Word x = 0;
                 bool keep = false;
                 if (r < c1) {
-                    keep = unrank(o, C, r, x);
-                    if (keep && job.strategy == kStratBitmap)
-                        keep = !((ld_cg(grp.bitmap + (x >> 5)) >> (x & 31u)) & 1u);
+                    if constexpr (kWide) {
+                        keep = unrank_wide(o, g_binom64, r, x);
+                    } else {
+                        keep = unrank(o, C, r, x);
+                        if (keep && job.strategy == kStratBitmap)
+                            keep = !((ld_cg(grp.bitmap + (x >> 5)) >> (x & 31u)) & 1u);
+                    }
                 }
                 na = block_append(s.bs, keep, x, (uint32_t)(r - R0), s.list_x, s.list_off, na);
             }
@@ -423,11 +439,11 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     if (nglob && u1 > nprev && u < nprev + nglob) {
                         const uint32_t lo = max(u, nprev) - nprev, hi = min(u1, nprev + nglob) - nprev;
                         if (job.orth)
-                            block_test<true, true>(s.list_x, na, s.dead, grp.store,
+                            block_test<true, true>(s.list_x, na, s.dead, store,
                                                    (uint32_t)Kprev - hi, (uint32_t)Kprev - lo, d,
                                                    my_tests);
                         else
-                            block_test<true, false>(s.list_x, na, s.dead, grp.store,
+                            block_test<true, false>(s.list_x, na, s.dead, store,
                                                     (uint32_t)Kprev - hi, (uint32_t)Kprev - lo, d,
                                                     my_tests);
                     }
@@ -453,7 +469,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             // publish this CTA's survivors and wait for the group
             {
                 const int par = seq & 1;
-                uint32_t* sx = grp.seg_x + ((size_t)par * G + lb) * kChunk;
+                Word* sx = seg_x + ((size_t)par * G + lb) * kChunk;
                 uint32_t* so = grp.seg_off + ((size_t)par * G + lb) * kChunk;
                 for (uint32_t i = tid; i < na; i += kBlock) {
                     sx[i] = s.list_x[i];
@@ -473,7 +489,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 const uint32_t p0 = s.pref[g];
                 if (p0 >= Suse) continue;
                 const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
-                const uint32_t* gx = grp.seg_x + ((size_t)par * G + g) * kChunk;
+                const Word* gx = seg_x + ((size_t)par * G + g) * kChunk;
                 const uint32_t* go = grp.seg_off + ((size_t)par * G + g) * kChunk;
                 for (uint32_t i = lane; i < cnt; i += 32) {
                     s.list_x[p0 + i] = ld_cg(gx + i);
@@ -501,14 +517,14 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             if (lb == 0) {
                 for (uint32_t i = tid; i < nacc; i += kBlock) {
                     const uint64_t pos = K + i;
-                    if (pos < job.cap) job.out[pos] = cur[i];
+                    if (pos < job.cap) static_cast<Word*>(job.out)[pos] = cur[i];
                     if (!o.filter && !o.even) dense += o.N - 1 - (R0 + s.acc_off[i]);
                 }
             }
             if (job.strategy == kStratDistance) {
                 for (uint32_t i = tid; i < nacc; i += kBlock) {
                     const uint64_t pos = K + i;
-                    if (lb == 0 && pos < grp.store_words) grp.store[pos] = cur[i];
+                    if (lb == 0 && pos < grp.store_words) store[pos] = cur[i];
                     if (pos < a.cache_words) cache[pos] = cur[i];
                 }
             }
@@ -520,7 +536,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 W = min(W * 2u, job.wmax);
             Kprev = K;
             K += nacc;
-            uint32_t* t = cur;
+            Word* t = cur;
             cur = prev;
             prev = t;
             nprev = nacc;
@@ -647,7 +663,17 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
         *why = "no jobs";
         return false;
     }
-    const size_t base = sizeof(SweepSmem);
+    // one wide job makes the whole launch wide (uint64 words, distance only)
+    bool wide = false;
+    for (int j = 0; j < njobs; ++j) wide = wide || jobs[j].wide;
+    for (int j = 0; j < njobs; ++j)
+        if (wide && jobs[j].plan.strategy != GC_STRATEGY_DISTANCE) {
+            *why = "the wide sweep (uint64 words) runs the distance strategy only";
+            return false;
+        }
+    L->wide = wide;
+    const size_t wbytes = wide ? 8 : 4;
+    const size_t base = wide ? sizeof(SweepSmem<uint64_t>) : sizeof(SweepSmem<uint32_t>);
     if ((size_t)optin < base + 16) {
         *why = "not enough shared memory per block";
         return false;
@@ -664,10 +690,10 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
     for (int j = 0; j < njobs; ++j)
         if (jobs[j].plan.strategy == GC_STRATEGY_DISTANCE)
             need_cache = std::max<uint64_t>(need_cache, jobs[j].p.bound);
-    uint64_t room = (((size_t)optin - base) / 4) & ~(uint64_t)31;
+    uint64_t room = (((size_t)optin - base) / wbytes) & ~(uint64_t)31;
     uint32_t cache = (uint32_t)std::min<uint64_t>(room, (need_cache + 31) & ~(uint64_t)31);
     L->cache_words = cache;
-    L->smem_bytes = base + (size_t)cache * 4;
+    L->smem_bytes = base + (size_t)cache * wbytes;
     std::vector<double> cost(njobs);
     for (int j = 0; j < njobs; ++j) cost[j] = job_cost(jobs[j].p, jobs[j].plan.strategy);
     L->first_cta.assign(ng, 0);
@@ -749,9 +775,9 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
         const int G = L->ncta[g];
         // one spare flag pair per group (used only by the wait-fault injection)
         L->g_flags[g] = off;  off += align_up(sizeof(unsigned long long) * 2 * (G + 1));
-        L->g_segx[g] = off;   off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
+        L->g_segx[g] = off;   off += align_up(wbytes * 2 * (size_t)G * kChunk);
         L->g_segoff[g] = off; off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
-        L->g_store[g] = off;  off += align_up(sizeof(uint32_t) * store);
+        L->g_store[g] = off;  off += align_up(wbytes * store);
         L->g_store_words[g] = store;
         L->g_bitmap[g] = off; off += align_up((bits + 31) / 32 * 4);
     }
@@ -812,9 +838,9 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         G.job_begin = L.job_begin[g];
         G.job_end = L.job_end[g];
         G.flags = reinterpret_cast<unsigned long long*>(ws + L.g_flags[g]);
-        G.seg_x = reinterpret_cast<uint32_t*>(ws + L.g_segx[g]);
+        G.seg_x = ws + L.g_segx[g];
         G.seg_off = reinterpret_cast<uint32_t*>(ws + L.g_segoff[g]);
-        G.store = reinterpret_cast<uint32_t*>(ws + L.g_store[g]);
+        G.store = ws + L.g_store[g];
         G.store_words = L.g_store_words[g];
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
     }
@@ -856,7 +882,9 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
             return rc;
         }
     }
-    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const void* kernel = L.wide ? (const void*)sweep_kernel<uint64_t>
+                                : (const void*)sweep_kernel<uint32_t>;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)L.smem_bytes)) != cudaSuccess)
         return cuda_fail("shared memory attribute");
     BatchArgs a{};
@@ -869,8 +897,8 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
     a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
     a.resolve_block = resolve_block_size();
     void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(L.grid), dim3(kBlock), args,
-                                    L.smem_bytes, stream);
+    e = cudaLaunchCooperativeKernel(kernel, dim3(L.grid), dim3(kBlock), args, L.smem_bytes,
+                                    stream);
     if (e != cudaSuccess) return cuda_fail("sweep launch");
     return GC_OK;
 }
@@ -889,7 +917,7 @@ bool serve_layout(const gc_server_config& cfg, ServeLayout* L, std::string* why)
         *why = "cannot query the CUDA device";
         return false;
     }
-    const size_t base = sizeof(SweepSmem);
+    const size_t base = sizeof(SweepSmem<uint32_t>);
     if ((size_t)optin < base + 16) {
         *why = "not enough shared memory per block";
         return false;
@@ -1017,9 +1045,9 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
         G.ncta = L.group_ctas;
         G.job_begin = G.job_end = 0;
         G.flags = reinterpret_cast<unsigned long long*>(ws + L.g_flags[g]);
-        G.seg_x = reinterpret_cast<uint32_t*>(ws + L.g_segx[g]);
+        G.seg_x = ws + L.g_segx[g];
         G.seg_off = reinterpret_cast<uint32_t*>(ws + L.g_segoff[g]);
-        G.store = reinterpret_cast<uint32_t*>(ws + L.g_store[g]);
+        G.store = ws + L.g_store[g];
         G.store_words = L.store_words;
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
     }
@@ -1042,7 +1070,8 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
     // is: a relaunch continues with the first published job no group has
     // claimed
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail("server set-up");
-    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(sweep_kernel<uint32_t>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)L.smem_bytes)) != cudaSuccess)
         return cuda_fail("shared memory attribute");
     BatchArgs a{};
@@ -1065,7 +1094,8 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
     a.queue.capacity = capacity;
     a.queue.idle_cycles = (long long)(idle_seconds * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);
     void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(L.grid), dim3(kBlock), args,
+    e = cudaLaunchCooperativeKernel((const void*)sweep_kernel<uint32_t>, dim3(L.grid),
+                                    dim3(kBlock), args,
                                     L.smem_bytes, stream);
     if (e != cudaSuccess) return cuda_fail("server launch");
     return GC_OK;

@@ -21,6 +21,8 @@ __all__ = [
     "GcError", "Problem", "Plan", "Stats", "lib", "library_path", "header_functions",
     "strerror", "candidate_count", "capacity_bound", "plan", "workspace_size",
     "generate", "generate_async", "generate_host",
+    "workspace_size64", "generate64", "generate64_async", "generate64_host",
+    "product", "selforth_product",
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
     "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
     "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
@@ -122,6 +124,12 @@ _SIGS = {
     "gc_set_tune_cache": (_i32, [ctypes.c_char_p]),
     "gc_batch_generate_async": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp]),
     "gc_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+    "gc_workspace_size64": (ctypes.c_size_t, [ctypes.POINTER(Problem), ctypes.POINTER(Plan)]),
+    "gc_product": (_i32, [_vp, _u64, _i32, _vp, _u64, _i32, _vp, _u64, _vp]),
+    "gc_product64": (_i32, [_vp, _u64, _i32, _vp, _u64, _i32, _vp, _u64, _vp]),
+    "gc_generate64": (_i32, [_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_u64)]),
+    "gc_generate64_async": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan), _vp, _u64, _vp,
+                                   _vp, ctypes.c_size_t, _vp]),
 }
 
 
@@ -349,8 +357,13 @@ def stats_from(t) -> Stats:
 
 def generate(n, d, ordering="lex", weight=NO_WEIGHT, *, strategy=None, stream=None,
              capacity=None, return_stats=False, constraint=None, **plan_kw):
-    """Whole sweep on the current CUDA device; returns a uint32 CUDA tensor
-    with the code in acceptance order (and the Stats if asked)."""
+    """Whole sweep on the current CUDA device; returns a CUDA tensor with the
+    code in acceptance order (and the Stats if asked): int32 words for
+    n <= 32, int64 words (the uint64 bit patterns, generate64) for n > 32."""
+    if n > 32:
+        return generate64(n, d, ordering, weight, strategy=strategy, stream=stream,
+                          capacity=capacity, return_stats=return_stats, constraint=constraint,
+                          **plan_kw)
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     cap = _bound(n, d, weight, constraint) if capacity is None else capacity
@@ -381,6 +394,98 @@ def generate_host(n, d, ordering="lex", weight=NO_WEIGHT, capacity=None) -> np.n
                            buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt))
     _check(rc, "gc_generate")
     return buf[:cnt.value].copy()
+
+
+# ---------------------------------------------------------------- wide vectors
+def workspace_size64(n, d, ordering="lex", weight=NO_WEIGHT, strategy=None, constraint=None,
+                     **plan_kw) -> int:
+    pl = _plan_arg(strategy, **plan_kw)
+    return int(lib().gc_workspace_size64(
+        ctypes.byref(_problem(n, d, ordering, weight, constraint)),
+        ctypes.byref(pl) if pl is not None else None))
+
+
+def generate64_async(n, d, ordering="lex", weight=NO_WEIGHT, *, out, stats, workspace,
+                     strategy=None, stream=None, constraint=None, **plan_kw):
+    """gc_generate64_async (n <= 64): out is an int64 CUDA tensor (uint64 bit
+    patterns; its length is the capacity), stats and workspace as for
+    generate_async (workspace_size64 bytes)."""
+    import torch
+    if out is not None and out.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("expected a CUDA tensor of 64-bit words")
+    pl = _plan_arg(strategy, **plan_kw)
+    rc = lib().gc_generate64_async(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
+                                   ctypes.byref(pl) if pl is not None else None,
+                                   _ptr(out), out.numel() if out is not None else 0, _ptr(stats),
+                                   _ptr(workspace), workspace.numel(), _stream(stream))
+    _check(rc, "gc_generate64_async")
+
+
+def generate64(n, d, ordering="lex", weight=NO_WEIGHT, *, strategy=None, stream=None,
+               capacity=None, return_stats=False, constraint=None, **plan_kw):
+    """Whole wide sweep (n <= 64); returns an int64 CUDA tensor holding the
+    uint64 codewords in acceptance order (and the Stats if asked)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cap = _bound(n, d, weight, constraint) if capacity is None else capacity
+    ws_bytes = workspace_size64(n, d, ordering, weight, strategy, constraint, **plan_kw)
+    if ws_bytes == 0:
+        raise GcError(1, "gc_workspace_size64")
+    out = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+    st = torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    base = (-ws.data_ptr()) % 256
+    generate64_async(n, d, ordering, weight, out=out[:cap] if cap else None, stats=st,
+                     workspace=ws[base:base + ws_bytes], strategy=strategy, stream=stream,
+                     constraint=constraint, **plan_kw)
+    s = stats_from(st)
+    if s.status != 0:
+        raise GcError(int(s.status), "sweep")
+    code = out[:min(s.codewords, cap)]
+    return (code, s) if return_stats else code
+
+
+def generate64_host(n, d, ordering="lex", weight=NO_WEIGHT, capacity=None) -> np.ndarray:
+    """gc_generate64 with a host buffer; returns uint64 words."""
+    cap = capacity_bound(n, d, weight) if capacity is None else capacity
+    buf = np.empty(max(cap, 1), dtype=np.uint64)
+    cnt = _u64(cap)
+    rc = lib().gc_generate64(n, d, _ord(ordering), weight,
+                             buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt))
+    _check(rc, "gc_generate64")
+    return buf[:cnt.value].copy()
+
+
+# ---------------------------------------------------------------- products
+def product(a, len_a: int, b, len_b: int, out=None, stream=None):
+    """gc_product / gc_product64 (Section 5, recursion for self-orthogonal
+    codes): every codeword of a (length len_a) followed by every codeword of b
+    (length len_b), a outermost.  a and b are CUDA tensors of one word width
+    (int32: len_a + len_b <= 32, int64: <= 64); returns a tensor of that
+    width with len(a) * len(b) words."""
+    import torch
+    if a.dtype != b.dtype or a.element_size() not in (4, 8) or not (a.is_cuda and b.is_cuda):
+        raise TypeError("expected two CUDA tensors of the same 32- or 64-bit word type")
+    a, b = a.contiguous(), b.contiguous()
+    total = a.numel() * b.numel()
+    if out is None:
+        out = torch.empty(max(total, 1), dtype=a.dtype, device=a.device)
+    f = lib().gc_product64 if a.element_size() == 8 else lib().gc_product
+    _check(f(_ptr(a), a.numel(), len_a, _ptr(b), b.numel(), len_b, _ptr(out), out.numel(),
+             _stream(stream)), "gc_product")
+    return out[:total]
+
+
+def selforth_product(n: int, d: int, k: int, stream=None):
+    """Code[n, d] built as Section 5 does: the lex self-orthogonal greedy code
+    of length n - k times the one of length k (both from the sweep, then one
+    gc_product).  Word width as generate() gives for length n."""
+    if not (1 <= k < n):
+        raise ValueError("need 1 <= k < n")
+    gen = generate64 if n > 32 else generate
+    a = gen(n - k, d, "lex", constraint="self_orthogonal", stream=stream)
+    b = gen(k, d, "lex", constraint="self_orthogonal", stream=stream)
+    return product(a, n - k, b, k, stream=stream)
 
 
 # ---------------------------------------------------------------- the steps

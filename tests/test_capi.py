@@ -28,7 +28,9 @@ def test_strerror_names_every_code():
 
 @pytest.mark.parametrize("n,w,ordname,want", [
     (10, -1, "lex", 1024), (32, -1, "gray", 1 << 32), (12, 5, "lex", comb(12, 5)),
-    (12, 5, "grevlex", comb(12, 5)), (12, 5, "gray", 4096), (0, -1, "lex", 0), (33, -1, "lex", 0),
+    (12, 5, "grevlex", comb(12, 5)), (12, 5, "gray", comb(12, 5)), (0, -1, "lex", 0),
+    (33, -1, "lex", 1 << 33), (40, 3, "gray", comb(40, 3)), (40, -1, "gray", 1 << 40), (35, 7, "grevlex", comb(35, 7)),
+    (64, 32, "grlex", comb(64, 32)), (64, -1, "lex", 0), (64, 3, "gray", comb(64, 3)), (12, 5, "basis", 4096), (65, 2, "lex", 0),
     (5, 6, "lex", 0), (5, -2, "lex", 0), (5, -1, 5, 0), (5, -1, 4, 32), (6, 3, 4, 64)])
 def test_candidate_count(n, w, ordname, want):
     assert G.candidate_count(n, w, ordname) == want
@@ -37,7 +39,9 @@ def test_candidate_count(n, w, ordname, want):
 @pytest.mark.parametrize("n,d,w,want", [
     (15, 3, -1, 2048), (7, 3, -1, 16), (23, 7, -1, 4096), (24, 8, -1, (1 << 24) // 2325),
     (10, 1, -1, 1024), (10, 0, -1, 1024), (10, 2, -1, 1024), (12, 4, 3, comb(12, 3)),
-    (32, 4, -1, (1 << 32) // 33), (5, -1, -1, 0)])
+    (32, 4, -1, (1 << 32) // 33), (5, -1, -1, 0), (40, 3, -1, (1 << 40) // 41),
+    (64, 4, 2, comb(64, 2)), (35, 8, 7, (1 << 35) // (1 + 35 + comb(35, 2) + comb(35, 3))),
+    (64, 3, -1, 0)])
 def test_capacity_bound(n, d, w, want):
     assert G.capacity_bound(n, d, w) == want
 
@@ -55,3 +59,12 @@ def test_argument_errors_without_gpu():
     assert L.gc_resolve(-1, None, 0, None, None, None) == 1
     assert L.gc_plan(None, None) == 1
     assert L.gc_generate_async(ctypes.byref(p), None, None, 0, None, None, 0, None) == 1
+    # wide vectors: n > 32 only through the gc_*64 entries
+    assert L.gc_generate(33, 3, 0, 2, None, ctypes.byref(cnt)) == 1
+    assert "64" in G.gc._last_error()
+    assert L.gc_generate64(65, 3, 0, 2, None, ctypes.byref(cnt)) == 1
+    assert L.gc_generate64(64, 3, 0, -1, None, ctypes.byref(cnt)) == 1   # 2^64 ranks
+    assert L.gc_generate64(64, 3, 1, -1, None, ctypes.byref(cnt)) == 1   # Gray, 2^64 ranks
+    assert L.gc_generate64(40, 3, 4, -1, None, ctypes.byref(cnt)) == 1   # no wide B-ordering
+    w = G.Problem(40, 3, 0, 4)
+    assert L.gc_generate64_async(ctypes.byref(w), None, None, 0, None, None, 0, None) == 1

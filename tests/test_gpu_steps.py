@@ -39,8 +39,6 @@ def test_unrank_and_rank(ordname):
         b = min(len(seq), a + 77)
         assert host(g.unrank(n, ordname, -1, a, b - a)).tolist() == seq[a:b].tolist()
         for w in (0, n // 2, n):
-            if ordname == "gray":
-                continue
             sub = oracle.order_list(n, ordname, w)
             assert host(g.unrank(n, ordname, w, 0, len(sub))).tolist() == sub.tolist()
 
@@ -92,10 +90,7 @@ def test_bitmap_scan(ordname):
     g = G()
     rng = np.random.default_rng(5)
     for n, w in [(9, -1), (16, -1), (16, 5), (20, 8)]:
-        if ordname == "gray" and w >= 0:
-            N = 1 << n
-        else:
-            N = (1 << n) if w < 0 else comb(n, w)
+        N = (1 << n) if w < 0 else comb(n, w)
         bm = (rng.integers(0, 1 << 32, max(1, (1 << n) // 32), dtype=np.uint64)
               & rng.integers(0, 1 << 32, max(1, (1 << n) // 32), dtype=np.uint64)).astype(np.uint32)
         for r0, cnt in [(0, N), (N // 5, N // 3), (N - 1, 1), (7, 0)]:

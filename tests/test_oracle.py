@@ -338,14 +338,14 @@ def test_step_scan(ordname):
     seq = oracle.order_list(n, ordname)
     want = [int(x) for x in seq[37:400] if not (int(bm[x >> 5]) >> (int(x) & 31)) & 1]
     assert oracle.scan(n, ordname, -1, bm, 37, 363).tolist() == want
-    # weight-restricted rank spaces
+    # weight-restricted rank spaces: rank i is the i-th weight-w vector of the
+    # full order
     w = 4
-    if ordname == "gray":
-        sub = [int(x) for x in seq if popc(x) == w]
-    else:
-        sub = oracle.order_list(n, ordname, w).tolist()
-    assert oracle.scan(n, ordname, w, empty, 0, len(seq) if ordname == "gray" else comb(n, w)) \
-        .tolist() == sub
+    sub = [int(x) for x in seq if popc(x) == w]
+    assert sub == oracle.order_list(n, ordname, w).tolist()
+    assert oracle.scan(n, ordname, w, empty, 0, comb(n, w)).tolist() == sub
+    sw = [x for x in sub[20:90] if not (int(bm[x >> 5]) >> (x & 31)) & 1]
+    assert oracle.scan(n, ordname, w, bm, 20, 70).tolist() == sw
 
 
 # ---------------------------------------------------------------- self-orthogonal

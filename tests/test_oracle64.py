@@ -3,7 +3,8 @@ constant-weight codes of Section 7 go to length 35).  Each check ties them to
 something other than themselves: the independently pinned 32-bit forms where
 the lengths overlap, the closed form of constant-weight codes whose distance
 forces disjoint supports, the prefix structure of the lex, Gray and grlex
-orders, and the O3 characterisation."""
+orders, and the O3 characterisation; the Cartesian product of codes (Section
+5) by the example the paper gives and by brute force."""
 from math import comb
 
 import numpy as np
@@ -101,3 +102,47 @@ def test_degenerate_64():
         assert len(seq) == comb(34, 2)
         assert oracle.greedy64(34, 1, ordname, 2).tolist() == seq.tolist()   # d <= 1: all
         assert oracle.greedy64(34, 40, ordname, 2).tolist() == seq[:1].tolist()  # d > n: first
+
+
+# ---------------------------------------------------------------- products
+def _min_distance(words):
+    w = [int(v) for v in words]
+    return min(bin(a ^ b).count("1") for i, a in enumerate(w) for b in w[:i])
+
+
+def _self_orthogonal(words):
+    w = [int(v) for v in words]
+    return all(bin(a).count("1") % 2 == 0 for a in w) and \
+        all(bin(a & b).count("1") % 2 == 0 for i, a in enumerate(w) for b in w[:i])
+
+
+def test_product_example_of_section5():
+    # the self-orthogonal greedy [8, 4] code combined with Code[4, 4] (the
+    # repetition code of length 4) gives a length-12 code of distance 4
+    A = oracle.greedy_selforth(8, 4, "lex")
+    assert len(A) == 16
+    B = [0, 0b1111]
+    P = oracle.product64(A, B, 8, 4)
+    assert len(P) == 32
+    assert all(int(v) < (1 << 12) for v in P)
+    assert _min_distance(P) == 4
+    assert _self_orthogonal(P)
+    # linear: the span has dimension 4 + 1
+    assert set(int(a) ^ int(b) for a in P for b in P) == set(int(v) for v in P)
+    # order: A outermost, B inner
+    assert [int(v) for v in P[:2]] == [int(A[0]) << 4, (int(A[0]) << 4) | 15]
+
+
+def test_product_distance_is_the_smaller_one_bruteforce():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        la, lb = int(rng.integers(3, 9)), int(rng.integers(3, 9))
+        A = np.unique(rng.integers(0, 1 << la, int(rng.integers(2, 8)))).astype(np.uint64)
+        B = np.unique(rng.integers(0, 1 << lb, int(rng.integers(2, 8)))).astype(np.uint64)
+        if len(A) < 2 or len(B) < 2:
+            continue
+        P = oracle.product64(A, B, la, lb)
+        assert len(P) == len(A) * len(B)
+        assert _min_distance(P) == min(_min_distance(A), _min_distance(B))
+    with pytest.raises(RuntimeError):
+        oracle.product64([1], [1], 40, 30)
