@@ -37,14 +37,14 @@ __device__ __forceinline__ uint32_t block_append(BlockScratch& bs, bool keep, W 
     if (lane == 0) bs.warp_sum[warp] = __popc(bal);
     __syncthreads();
     if (warp == 0) {
-        const uint32_t v = bs.warp_sum[lane];
+        const uint32_t v = lane < kWarps ? bs.warp_sum[lane] : 0u;
         uint32_t incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += t;
         }
-        bs.warp_sum[lane] = incl - v;
+        if (lane < kWarps) bs.warp_sum[lane] = incl - v;
         if (lane == 31) bs.warp_sum[kWarps] = incl;
     }
     __syncthreads();
@@ -274,48 +274,54 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
         tick(0);
         if (threadIdx.x < 3) bs.left[threadIdx.x] = 0u;
         __syncthreads();
-        for (uint32_t round = 0;; ++round) {
-            if (timing) tim[3] += 1;
-            // slot of this round's flag; the next round's slot is cleared here:
-            // it was last read two rounds ago, and every thread has passed the
-            // previous round's first barrier since then
-            const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
-            if (threadIdx.x == 0) bs.left[next] = 0u;
-            unsigned ba = 0, br = 0;
-            if ((uint32_t)warp < nwords && bs.und[warp] != 0u) {
-                const uint32_t i = warp * 32u + lane;
-                const bool u = (bs.und[warp] >> lane) & 1u;
-                bool a_now = false, r_now = false;
-                if (u) {
-                    bool killed = false, blocked = false;
-                    const uint4* acc4 = reinterpret_cast<const uint4*>(bs.accb);
-                    const uint4* und4 = reinterpret_cast<const uint4*>(bs.und);
-                    for (uint32_t w4 = 0; w4 * 4u <= (uint32_t)warp; ++w4) {
-                        const uint4 av = acc4[w4], uv = und4[w4];
-                        const uint32_t wb = w4 * 4u;
-                        const uint32_t m0 = Mt[wb][i];
-                        const uint32_t m1 = wb + 1 <= (uint32_t)warp ? Mt[wb + 1][i] : 0u;
-                        const uint32_t m2 = wb + 2 <= (uint32_t)warp ? Mt[wb + 2][i] : 0u;
-                        const uint32_t m3 = wb + 3 <= (uint32_t)warp ? Mt[wb + 3][i] : 0u;
-                        killed |= ((m0 & av.x) | (m1 & av.y) | (m2 & av.z) | (m3 & av.w)) != 0u;
-                        blocked |= ((m0 & uv.x) | (m1 & uv.y) | (m2 & uv.z) | (m3 & uv.w)) != 0u;
+        // the rounds involve only the warps that own rows (barrier 1 over
+        // them); the rest wait at the CTA barrier after the loop
+        if ((uint32_t)warp < nwords) {
+            const unsigned nthreads = nwords * 32u;
+            for (uint32_t round = 0;; ++round) {
+                if (timing) tim[3] += 1;
+                // slot of this round's flag; the next round's slot is cleared
+                // here: it was last read two rounds ago, and every thread of
+                // the rounds has passed the previous round's first barrier
+                const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
+                if (threadIdx.x == 0) bs.left[next] = 0u;
+                unsigned ba = 0, br = 0;
+                if (bs.und[warp] != 0u) {
+                    const uint32_t i = warp * 32u + lane;
+                    const bool u = (bs.und[warp] >> lane) & 1u;
+                    bool a_now = false, r_now = false;
+                    if (u) {
+                        bool killed = false, blocked = false;
+                        const uint4* acc4 = reinterpret_cast<const uint4*>(bs.accb);
+                        const uint4* und4 = reinterpret_cast<const uint4*>(bs.und);
+                        for (uint32_t w4 = 0; w4 * 4u <= (uint32_t)warp; ++w4) {
+                            const uint4 av = acc4[w4], uv = und4[w4];
+                            const uint32_t wb = w4 * 4u;
+                            const uint32_t m0 = Mt[wb][i];
+                            const uint32_t m1 = wb + 1 <= (uint32_t)warp ? Mt[wb + 1][i] : 0u;
+                            const uint32_t m2 = wb + 2 <= (uint32_t)warp ? Mt[wb + 2][i] : 0u;
+                            const uint32_t m3 = wb + 3 <= (uint32_t)warp ? Mt[wb + 3][i] : 0u;
+                            killed |= ((m0 & av.x) | (m1 & av.y) | (m2 & av.z) | (m3 & av.w)) != 0u;
+                            blocked |= ((m0 & uv.x) | (m1 & uv.y) | (m2 & uv.z) | (m3 & uv.w)) != 0u;
+                        }
+                        r_now = killed;
+                        a_now = !killed && !blocked;
                     }
-                    r_now = killed;
-                    a_now = !killed && !blocked;
+                    ba = __ballot_sync(kFull, a_now);
+                    br = __ballot_sync(kFull, r_now);
                 }
-                ba = __ballot_sync(kFull, a_now);
-                br = __ballot_sync(kFull, r_now);
+                named_barrier(1, nthreads);
+                if (lane == 0) {
+                    bs.accb[warp] |= ba;
+                    const uint32_t und = bs.und[warp] & ~(ba | br);
+                    bs.und[warp] = und;
+                    if (und) bs.left[slot] = 1u;
+                }
+                named_barrier(1, nthreads);
+                if (bs.left[slot] == 0u) break;
             }
-            __syncthreads();
-            if (lane == 0 && (uint32_t)warp < nwords) {
-                bs.accb[warp] |= ba;
-                const uint32_t und = bs.und[warp] & ~(ba | br);
-                bs.und[warp] = und;
-                if (und) bs.left[slot] = 1u;
-            }
-            __syncthreads();
-            if (bs.left[slot] == 0u) break;
         }
+        __syncthreads();
         tick(1);
         // append the block's accepts in order
         const uint32_t nacc0 = nacc;

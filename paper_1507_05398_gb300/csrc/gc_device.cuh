@@ -302,6 +302,11 @@ __device__ __forceinline__ uint64_t ld_cg(const uint64_t* p) {
 
 // ---------------------------------------------------------------- warp utils
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+// Barrier `id` (1..15; 0 is __syncthreads) over the first nthreads threads
+// of the CTA (a multiple of 32; every one of them must call it).
+__device__ __forceinline__ void named_barrier(unsigned id, unsigned nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
 }  // namespace gc

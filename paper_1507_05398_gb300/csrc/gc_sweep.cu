@@ -145,14 +145,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(BlockScratch& bs, uint3
     if (lane == 31) bs.warp_sum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const uint32_t w = bs.warp_sum[lane];
+        const uint32_t w = lane < kWarps ? bs.warp_sum[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, wi, o);
             if (lane >= o) wi += t;
         }
-        bs.warp_sum[lane] = wi - w;
+        if (lane < kWarps) bs.warp_sum[lane] = wi - w;
         if (lane == 31) bs.warp_sum[kWarps] = wi;
     }
     __syncthreads();
