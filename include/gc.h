@@ -255,6 +255,26 @@ int gc_batch_generate_async(const gc_job *jobs, int njobs, int ngroups,
                             void *workspace, size_t workspace_bytes,
                             void *stream);
 
+/* Batches launched many times (and CUDA graphs).  gc_batch_create does the
+ * host work of gc_batch_generate_async once: it checks and plans the jobs,
+ * lays out the workspace and fills it on `stream` (job and group
+ * descriptors, ball tables), and returns a handle.  The workspace (>=
+ * gc_batch_workspace_size bytes, 256-byte aligned) and the jobs' d_out and
+ * d_stats buffers stay owned by the caller and must outlive the handle.
+ * gc_batch_launch then runs the batch on `stream`: it resets the per-launch
+ * state in the workspace (memsets of the error word and of each group's
+ * flags) and launches the persistent sweep,
+ * nothing else -- only stream operations, so it can be captured into a CUDA
+ * graph (stream capture) and the graph replayed.  Each run overwrites the
+ * outputs and stats with the same codes.  Runs of one handle must not
+ * overlap (they share the workspace).  gc_batch_destroy frees the host
+ * handle only.  Errors as for gc_batch_generate_async. */
+typedef struct gc_batch gc_batch;
+int gc_batch_create(const gc_job *jobs, int njobs, int ngroups, void *workspace,
+                    size_t workspace_bytes, void *stream, gc_batch **out);
+int gc_batch_launch(gc_batch *b, void *stream);
+int gc_batch_destroy(gc_batch *b);
+
 /* ---- serving: requests admitted while others run ------------------------ */
 
 /* Server settings (zero fields take the defaults in brackets). */

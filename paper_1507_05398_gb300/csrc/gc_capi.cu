@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -480,6 +481,57 @@ int gc_batch_generate_async(const gc_job* jobs, int njobs, int ngroups, void* wo
         return fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
     rc = launch_batch(B.data(), njobs, L, workspace, (cudaStream_t)stream, &why);
     return rc ? fail(rc, why) : GC_OK;
+}
+
+}  // extern "C"
+
+// A prepared batch: jobs checked and planned, workspace laid out and filled.
+struct gc_batch {
+    std::vector<BatchJob> jobs;
+    BatchLayout L;
+    void* ws = nullptr;
+};
+
+extern "C" {
+
+int gc_batch_create(const gc_job* jobs, int njobs, int ngroups, void* workspace,
+                    size_t workspace_bytes, void* stream, gc_batch** out) {
+    if (!out) return fail(GC_ERR_INVALID, "null handle pointer");
+    *out = nullptr;
+    gc_batch* b = new (std::nothrow) gc_batch();
+    if (!b) return fail(GC_ERR_OOM, "host allocation");
+    int rc = make_batch(jobs, njobs, &b->jobs);
+    std::string why;
+    if (!rc && !batch_layout(b->jobs.data(), njobs, ngroups, &b->L, &why))
+        rc = fail(GC_ERR_UNSUPPORTED, why);
+    if (!rc && (!workspace || workspace_bytes < b->L.total))
+        rc = fail(GC_ERR_INVALID, "workspace too small");
+    if (!rc && ((uintptr_t)workspace & 255u) != 0)
+        rc = fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
+    if (!rc) {
+        b->ws = workspace;
+        const int r = upload_batch(b->jobs.data(), njobs, b->L, workspace, (cudaStream_t)stream,
+                                   &why);
+        if (r) rc = fail(r, why);
+    }
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return GC_OK;
+}
+
+int gc_batch_launch(gc_batch* b, void* stream) {
+    if (!b) return fail(GC_ERR_INVALID, "null handle");
+    std::string why;
+    const int rc = launch_batch_kernel(b->L, b->ws, (cudaStream_t)stream, &why);
+    return rc ? fail(rc, why) : GC_OK;
+}
+
+int gc_batch_destroy(gc_batch* b) {
+    delete b;
+    return GC_OK;
 }
 
 int gc_unrank(int n, int ordering, int w, uint64_t rank0, uint64_t count, uint32_t* d_vec,

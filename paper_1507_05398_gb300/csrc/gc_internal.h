@@ -115,9 +115,16 @@ struct BatchLayout {
 bool batch_layout(const BatchJob* jobs, int njobs, int ngroups, BatchLayout* L, std::string* why);
 
 // Launches the batched sweep (descriptor copies, set-up kernels, the
-// cooperative sweep) on stream; returns a GC_* code.
+// cooperative sweep) on stream; returns a GC_* code.  It is upload_batch
+// (descriptors, ball tables, kernel attributes: once per batch) followed by
+// launch_batch_kernel (per-launch state reset and the persistent kernel:
+// stream operations only, so it can be captured into a CUDA graph).
 int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
                  cudaStream_t stream, std::string* why);
+int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
+                 cudaStream_t stream, std::string* why);
+int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stream,
+                        std::string* why);
 
 // Step launchers (gc_steps.cu); each returns a GC_* code.
 int launch_unrank(const HostProblem& p, uint64_t rank0, uint64_t count, uint32_t* d_vec,

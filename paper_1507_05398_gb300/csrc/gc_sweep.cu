@@ -797,14 +797,18 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
     return true;
 }
 
-int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
+// Host-side fault injection for tests of the failure path: GC_FAULT=wait
+// makes group 0 wait for one CTA that does not exist, with a 0.2 s limit, so
+// its bounded waits expire and every job reports GC_ERR_TIMEOUT.
+static bool inject_wait_fault() {
+    const char* fault = std::getenv("GC_FAULT");
+    return fault && std::strcmp(fault, "wait") == 0;
+}
+
+int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
                  cudaStream_t stream, std::string* why) {
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    // Host-side fault injection for tests of the failure path: GC_FAULT=wait
-    // makes group 0 wait for one CTA that does not exist, with a 0.2 s limit,
-    // so its bounded waits expire and every job reports GC_ERR_TIMEOUT.
-    const char* fault = std::getenv("GC_FAULT");
-    const bool inject_wait = fault && std::strcmp(fault, "wait") == 0;
+    const bool inject_wait = inject_wait_fault();
     std::vector<JobDesc> jd(njobs);
     for (int j = 0; j < njobs; ++j) {
         const BatchJob& J = jobs[j];
@@ -859,15 +863,6 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
     if ((e = cudaMemcpyAsync(ws + L.off_groups, gd.data(), sizeof(GroupDesc) * L.ngroups,
                              cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return cuda_fail("group descriptors");
-    if ((e = cudaMemsetAsync(ws + L.off_err, 0, 256, stream)) != cudaSuccess)
-        return cuda_fail("error word");
-    for (int g = 0; g < L.ngroups; ++g) {
-        // flags start at sequence 0xffffffff so no stale value matches
-        if ((e = cudaMemsetAsync(ws + L.g_flags[g], 0xff,
-                                 sizeof(unsigned long long) * 2 * (L.ncta[g] + 1), stream)) !=
-            cudaSuccess)
-            return cuda_fail("group flags");
-    }
     for (int j = 0; j < njobs; ++j) {
         if (jd[j].strategy != kStratBitmap) continue;
         bool first = true;
@@ -887,6 +882,29 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)L.smem_bytes)) != cudaSuccess)
         return cuda_fail("shared memory attribute");
+    return GC_OK;
+}
+
+int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stream,
+                        std::string* why) {
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    const bool inject_wait = inject_wait_fault();
+    cudaError_t e;
+    auto cuda_fail = [&](const char* what) {
+        *why = std::string(what) + ": " + cudaGetErrorString(e);
+        return GC_ERR_CUDA;
+    };
+    if ((e = cudaMemsetAsync(ws + L.off_err, 0, 256, stream)) != cudaSuccess)
+        return cuda_fail("error word");
+    for (int g = 0; g < L.ngroups; ++g) {
+        // flags start at sequence 0xffffffff so no stale value matches
+        if ((e = cudaMemsetAsync(ws + L.g_flags[g], 0xff,
+                                 sizeof(unsigned long long) * 2 * (L.ncta[g] + 1), stream)) !=
+            cudaSuccess)
+            return cuda_fail("group flags");
+    }
+    const void* kernel = L.wide ? (const void*)sweep_kernel<uint64_t>
+                                : (const void*)sweep_kernel<uint32_t>;
     BatchArgs a{};
     a.jobs = reinterpret_cast<const JobDesc*>(ws + L.off_jobs);
     a.job_order = reinterpret_cast<const int*>(ws + L.off_order);
@@ -901,6 +919,12 @@ int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
                                     stream);
     if (e != cudaSuccess) return cuda_fail("sweep launch");
     return GC_OK;
+}
+
+int launch_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* workspace,
+                 cudaStream_t stream, std::string* why) {
+    const int rc = upload_batch(jobs, njobs, L, workspace, stream, why);
+    return rc ? rc : launch_batch_kernel(L, workspace, stream, why);
 }
 
 }  // namespace gc

@@ -123,6 +123,10 @@ _SIGS = {
                            ctypes.POINTER(ctypes.c_double)]),
     "gc_set_tune_cache": (_i32, [ctypes.c_char_p]),
     "gc_batch_generate_async": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp]),
+    "gc_batch_create": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp,
+                               ctypes.POINTER(ctypes.c_void_p)]),
+    "gc_batch_launch": (_i32, [_vp, _vp]),
+    "gc_batch_destroy": (_i32, [_vp]),
     "gc_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "gc_workspace_size64": (ctypes.c_size_t, [ctypes.POINTER(Problem), ctypes.POINTER(Plan)]),
     "gc_product": (_i32, [_vp, _u64, _i32, _vp, _u64, _i32, _vp, _u64, _vp]),
@@ -286,10 +290,12 @@ _STRAT = {None: 0, "auto": 0, "distance": 1, "bitmap": 2}
 
 
 class BatchBuffers:
-    """Device buffers (outputs, stats, workspace) for a batch of problems.
+    """Device buffers (outputs, stats, workspace) for a batch of problems,
+    prepared once (gc_batch_create) and launched any number of times
+    (gc_batch_launch), directly or as a captured CUDA graph.
 
-    problems: list of (n, d, ordering, weight[, strategy]).  Allocated once
-    (through torch's caching allocator) and reusable for repeated launches."""
+    problems: list of (n, d, ordering, weight[, strategy[, constraint]]).
+    Allocated once through torch's caching allocator."""
 
     def __init__(self, problems, ngroups=0, device=None):
         import torch
@@ -315,9 +321,31 @@ class BatchBuffers:
         base = (-ws.data_ptr()) % 256
         self._ws_alloc = ws
         self.workspace = ws[base:base + ws_bytes]
+        self._handle = ctypes.c_void_p()
+        _check(lib().gc_batch_create(self.jobs, len(self.jobs), ngroups, _ptr(self.workspace),
+                                     self.workspace.numel(), _stream(None),
+                                     ctypes.byref(self._handle)), "gc_batch_create")
+        # launches may come on any stream: the workspace is filled first
+        torch.cuda.current_stream().synchronize()
 
     def launch(self, stream=None):
-        batch_generate_async(self.jobs, self.ngroups, self.workspace, stream=stream)
+        """gc_batch_launch: one run of the whole batch (one kernel launch)."""
+        _check(lib().gc_batch_launch(self._handle, _stream(stream)), "gc_batch_launch")
+
+    def capture(self):
+        """A torch.cuda.CUDAGraph holding one launch of the batch; replay()
+        reruns it with no host work."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.launch()
+        return g
+
+    def __del__(self):
+        h = getattr(self, "_handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.gc_batch_destroy(h)
+            self._handle = None
 
     def results(self):
         """[(code uint32 numpy array, Stats)] after the stream has finished."""

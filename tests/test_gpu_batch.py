@@ -1,5 +1,6 @@
-"""The batched sweep (gc_batch_generate_async): every job's code equals the
-oracle's, whatever the grouping of SMs and the mix of jobs around it."""
+"""The batched sweep (gc_batch_generate_async, gc_batch_create/launch and
+its CUDA-graph replay): every job's code equals the oracle's, whatever the
+grouping of SMs, the mix of jobs around it and the number of relaunches."""
 import hashlib
 import json
 import os
@@ -29,6 +30,32 @@ def test_bench_workload_as_one_batch(ngroups):
         want, pos = oracle.greedy_ball(n, d, o, w, with_pos=True)
         assert code.tolist() == want.tolist(), (n, d, o, ngroups)
         assert st.dense_tests == oracle.dense_tests(pos, 1 << n)
+
+
+def test_batch_handle_relaunch_and_cuda_graph():
+    """gc_batch_create once, then gc_batch_launch several times, then the
+    launch captured into a CUDA graph and replayed: every run rewrites the
+    outputs with the oracle's codes."""
+    import torch
+    g = G()
+    buf = g.BatchBuffers(BENCH)
+    want = [oracle.greedy_ball(n, d, o, w).tolist() for n, d, o, w in BENCH]
+    for _ in range(2):
+        for t in buf.outs:
+            t.fill_(-1)
+        buf.launch()
+        torch.cuda.synchronize()
+        assert [c.tolist() for c, _ in buf.results()] == want
+    graph = buf.capture()
+    for _ in range(3):
+        for t in buf.outs:
+            t.fill_(-1)
+        buf.stats.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        res = buf.results()
+        assert all(st.status == 0 for _, st in res)
+        assert [c.tolist() for c, _ in res] == want
 
 
 def test_mixed_small_batch_each_job_alone_and_in_the_mix():
