@@ -2,7 +2,7 @@
  * gc.h -- C ABI of libgc, a GB300 (sm_103a) library for the ordered greedy
  * construction of binary codes.
  *
- * The method (Section 3, "Greedy Algorithms and Different Orderings"): order
+ * The method (Section 4, "Greedy Algorithms and Different Orderings"): order
  * the vectors of F_2^n, optionally only those of weight w; walk the order from
  * its first vector (the zero vector when no weight is given) and append a
  * vector to the code C iff its Hamming distance to every codeword already in C
@@ -186,7 +186,7 @@ int gc_set_tune_cache(const char *path);
  * plan (plan NULL = gc_plan()'s choice).  0 on invalid arguments. */
 size_t gc_workspace_size(const gc_problem *prob, const gc_plan_t *plan);
 
-/* Generate the greedy code (Section 3) on the current device, synchronously.
+/* Generate the greedy code (Section 4) on the current device, synchronously.
  *   out_codewords  host or device buffer of *inout_count uint32_t words;
  *                  receives the code in acceptance (= rank) order.
  *   inout_count    in: capacity in words; out: |C|.
@@ -243,7 +243,7 @@ typedef struct {
  * ngroups as for gc_batch_generate_async. */
 size_t gc_batch_workspace_size(const gc_job *jobs, int njobs, int ngroups);
 
-/* Generates every job's code (Section 3) in ONE persistent cooperative
+/* Generates every job's code (Section 4) in ONE persistent cooperative
  * launch.  The SMs are split into ngroups groups of equal size (ngroups <= 0:
  * one group per job, at most one per SM); jobs are assigned to groups longest
  * first (by an estimate of their work) and each group sweeps its jobs one
@@ -299,7 +299,7 @@ typedef struct gc_server gc_server;
  * other work on the device waits for it. */
 int gc_server_create(const gc_server_config *cfg, gc_server **out);
 
-/* Admits one request (Section 3 problem) if a ring slot is free and its
+/* Admits one request (Section 4 problem) if a ring slot is free and its
  * output -- gc_capacity_bound words -- fits in the pool (first fit);
  * otherwise returns GC_ERR_CAPACITY and the caller retries after releasing
  * finished requests.  strategy: gc_strategy.  Non-blocking. */
@@ -387,7 +387,7 @@ int gc_block_test(int d, const uint32_t *d_cand, uint64_t ncand,
                   const uint32_t *d_code, uint64_t ncode, uint8_t *d_alive,
                   void *stream);
 
-/* Step 3, in-order resolve (Section 3 restricted to a list): given
+/* Step 3, in-order resolve (Section 4 restricted to a list): given
  * candidates already known to clear every earlier codeword, accept them in
  * list order exactly as the serial sweep would: d_accepted[k] = list index of
  * the k-th accepted candidate, *d_count = number accepted.  ncand <= 65536.

@@ -162,7 +162,7 @@ def _greedy(fn, n, d, ordering, w, with_pos):
 
 
 def greedy_pairwise(n: int, d: int, ordering="lex", w: int = -1, with_pos: bool = False):
-    """O1: each candidate against every codeword so far (Section 3)."""
+    """O1: each candidate against every codeword so far (Section 4)."""
     return _greedy(_load().orc_greedy_pairwise, n, d, ordering, w, with_pos)
 
 
@@ -269,7 +269,7 @@ def order_list64(n: int, ordering, w: int = -1) -> np.ndarray:
 
 def greedy64(n: int, d: int, ordering="lex", w: int = -1, orth: bool = False,
              with_pos: bool = False):
-    """The greedy of Section 3 for n <= 64 (orth: with the Section 4.4
+    """The greedy of Section 4 for n <= 64 (orth: with the Section 4.4
     constraint), pairwise over the sorted candidate list."""
     cap = max(min(candidate_count64(n, w), 1 << 26), 1)
     out = np.empty(cap, dtype=np.uint64)

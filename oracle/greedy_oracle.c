@@ -8,7 +8,7 @@
  * of the benchmark use it.  It shares no code, header, table or helper with the
  * CUDA path.
  *
- * What it computes (Section 3, "Greedy Algorithms and Different Orderings"):
+ * What it computes (Section 4, "Greedy Algorithms and Different Orderings"):
  * order all vectors of F_2^n (optionally only those of weight w), then walk the
  * order starting from the zero vector and append a vector to the code C iff its
  * Hamming distance to every codeword already in C is at least d.  The result is
@@ -341,7 +341,7 @@ void orc_block_test(int d, const uint32_t *cand, int64_t nc, const uint32_t *cod
     }
 }
 
-/* In-order resolve: the greedy of Section 3 applied to a given list (the list
+/* In-order resolve: the greedy of Section 4 applied to a given list (the list
  * takes the place of the ordered space).  Writes the list indices of the
  * accepted entries; returns how many. */
 int64_t orc_resolve(int d, const uint32_t *cand, int64_t nc, int64_t *acc_idx) {
@@ -395,7 +395,7 @@ int64_t orc_scan(int n, int ord, int w, const uint32_t *bitmap, uint64_t rank0,
 }
 
 /* ---- self-orthogonal greedy codes (Section 4.4) ------------------------- */
-/* The greedy of Section 3 with the extra constraint of Section 4.4: a vector
+/* The greedy of Section 4 with the extra constraint of Section 4.4: a vector
  * is appended only if it is orthogonal to itself and to every codeword so
  * far (over F_2, x.y = popcount(x AND y) mod 2), besides being at distance
  * >= d from every codeword.  Pairwise form. */
@@ -454,7 +454,7 @@ uint32_t orc_border_vector(int n, const uint32_t *basis, uint64_t r) {
     return v;
 }
 
-/* The greedy of Section 3 over a B-ordering (optionally only weight-w
+/* The greedy of Section 4 over a B-ordering (optionally only weight-w
  * vectors, skipped in place like GRAY), pairwise form. */
 int64_t orc_greedy_border(int n, int d, const uint32_t *basis, int w, uint32_t *out,
                           int64_t *pos, int64_t cap) {
@@ -483,7 +483,7 @@ int64_t orc_greedy_border(int n, int d, const uint32_t *basis, int w, uint32_t *
 }
 
 /* ---- vectors of up to 64 coordinates ------------------------------------ */
-/* The same greedy for 1 <= n <= 64 (Section 3; the constant-weight codes of
+/* The same greedy for 1 <= n <= 64 (Section 4; the constant-weight codes of
  * Section 7 go to length 35).  Vectors are the low n bits of a uint64 with
  * coordinate 1 the most significant of them.  These forms materialise the
  * candidate list by the definition of the order: every candidate (the
@@ -582,7 +582,7 @@ int64_t orc64_order_list(int n, int ord, int w, uint64_t *out, int64_t cap) {
     return k;
 }
 
-/* The greedy of Section 3 (orth = 1: with the Section 4.4 constraint),
+/* The greedy of Section 4 (orth = 1: with the Section 4.4 constraint),
  * pairwise, over the sorted candidate list.  Writes up to cap codewords and
  * their candidate indices; returns |C|. */
 int64_t orc64_greedy(int n, int d, int ord, int w, int orth, uint64_t *out, int64_t *pos,

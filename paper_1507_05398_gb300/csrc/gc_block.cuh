@@ -185,7 +185,7 @@ __device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, W* x, uint32_
 // ------------------------------------------------------------ resolver
 // CTA-wide.  In-order resolution of a list of candidates that have all
 // cleared every codeword committed before them: accept them exactly as the
-// serial sweep would (Section 3).  Works on blocks of kResolveBlock
+// serial sweep would (Section 4).  Works on blocks of kResolveBlock
 // candidates: inside a block a bit matrix row i holds the earlier block
 // entries within distance d-1 of entry i, and rounds decide every entry whose
 // earlier conflicting entries are all decided -- rejected if one of them was

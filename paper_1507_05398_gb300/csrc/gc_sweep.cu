@@ -1,5 +1,5 @@
 // gc_sweep.cu -- the persistent windowed sweep: the ordered greedy
-// construction of Section 3 for one code or a batch of codes in one
+// construction of Section 4 for one code or a batch of codes in one
 // cooperative launch.
 //
 // The CTAs (one per SM) are split into groups; each group sweeps its own
