@@ -167,7 +167,7 @@ uint64_t gc_capacity_bound(int n, int d, int weight_or_none);
 int gc_plan(const gc_problem *prob, gc_plan_t *out_plan);
 
 /* Measured choice: runs the candidate plans (distance or bitmap strategy,
- * survivor targets 256/512/1024, all / a quarter / an eighth of the SMs) for
+ * survivor targets 256/512/1024/2048, all / a quarter / an eighth of the SMs) for
  * this problem on the current device, returns the fastest in *best and its
  * time in *best_ms (may be NULL), and appends it to the tuning cache if one
  * is installed.  Synchronous; allocates its own scratch.  GC_ORDER_BASIS

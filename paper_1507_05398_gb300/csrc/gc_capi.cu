@@ -152,7 +152,7 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
     pl->block = 1024;
     pl->window_min = 256;
     pl->window_max = 0;
-    pl->survivor_target = 256;
+    pl->survivor_target = kTargetDistance;
     // orthogonality cannot be marked in a bitmap; n > 32 has no bitmap form
     if (p.d <= 1 || p.orth || p.n > kMaxN) {
         pl->strategy = GC_STRATEGY_DISTANCE;
@@ -175,12 +175,11 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
         pl->strategy = GC_STRATEGY_BITMAP;
     else
         pl->strategy = GC_STRATEGY_DISTANCE;
-    // bitmap windows carry no old-code scan, so larger windows (more
-    // survivors per group exchange) pay off there (measured on GB300)
-    if (pl->strategy == GC_STRATEGY_BITMAP) pl->survivor_target = 512;
+    pl->survivor_target = default_target(pl->strategy);
     if (const char* e = std::getenv("GC_STRATEGY")) {
         if (!std::strcmp(e, "distance")) pl->strategy = GC_STRATEGY_DISTANCE;
         if (!std::strcmp(e, "bitmap")) pl->strategy = GC_STRATEGY_BITMAP;
+        pl->survivor_target = default_target(pl->strategy);
     }
 }
 
@@ -189,7 +188,7 @@ static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* o
     if (in) {
         if (in->strategy != GC_STRATEGY_AUTO && !p.orth) {
             out->strategy = in->strategy;
-            out->survivor_target = in->strategy == GC_STRATEGY_BITMAP ? 512 : 256;
+            out->survivor_target = default_target(in->strategy);
         }
         if (in->grid > 0) out->grid = in->grid;
         if (in->window_min) out->window_min = in->window_min;
@@ -206,7 +205,8 @@ static bool resolve_plan_wide(const HostProblem& p, const gc_plan_t* in, gc_plan
     if (out->strategy == GC_STRATEGY_BITMAP) {
         if (in && in->strategy == GC_STRATEGY_BITMAP) return false;
         out->strategy = GC_STRATEGY_DISTANCE;
-        out->survivor_target = (in && in->survivor_target) ? in->survivor_target : 256;
+        out->survivor_target =
+            (in && in->survivor_target) ? in->survivor_target : kTargetDistance;
     }
     return true;
 }

@@ -26,6 +26,16 @@ struct HostProblem {
     uint64_t bound;    // gc_capacity_bound
 };
 
+// Default survivors per window (the window size adapts to about this many):
+// the bitmap windows carry no old-code scan, so they take more survivors per
+// group exchange; both measured on GB300 (n = 20, d = 4 in four orders and
+// n = 24, d = 8 lex, with 16-152 CTAs per code).
+constexpr uint32_t kTargetDistance = 512;
+constexpr uint32_t kTargetBitmap = 1024;
+inline uint32_t default_target(int strategy) {
+    return strategy == GC_STRATEGY_BITMAP ? kTargetBitmap : kTargetDistance;
+}
+
 uint64_t binom64(int n, int k);
 bool make_problem(int n, int d, int ord, int w, HostProblem* out, std::string* why,
                   int constraint = GC_CONSTRAINT_NONE, const uint32_t* basis = nullptr,

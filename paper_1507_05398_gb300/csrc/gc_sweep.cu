@@ -823,7 +823,8 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         D.hball = D.strategy == kStratBitmap ? reinterpret_cast<const uint32_t*>(ws + L.hball_off[j])
                                              : nullptr;
         D.hball_len = D.strategy == kStratBitmap ? (uint32_t)high_ball_len(J.p.n, J.p.d) : 0u;
-        D.target = J.plan.survivor_target ? J.plan.survivor_target : 256;
+        D.target = J.plan.survivor_target ? J.plan.survivor_target
+                                          : default_target(J.plan.strategy);
         // a window never holds more candidates than the group's chunks
         int g = 0;
         for (int q = 0; q < L.ngroups; ++q)
@@ -1024,7 +1025,7 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
     D->out = d_out;
     D->cap = cap;
     D->stats = d_stats;
-    D->target = D->strategy == kStratBitmap ? 512 : 256;
+    D->target = default_target(pl.strategy);
     D->wmax = (uint32_t)((uint64_t)L.group_ctas * kChunk);
     D->wmin = std::min<uint32_t>(256, D->wmax);
     if (D->strategy == kStratBitmap && p.d >= 1) {

@@ -131,7 +131,7 @@ int gc_autotune(const gc_problem* prob, gc_plan_t* best, double* best_ms) {
     gc_plan_t base{};
     plan_for(p, &base);
     const int strategies[2] = {GC_STRATEGY_DISTANCE, GC_STRATEGY_BITMAP};
-    const uint32_t targets[3] = {256, 512, 1024};
+    const uint32_t targets[4] = {256, 512, 1024, 2048};
     const int grids[3] = {sms, std::max(1, sms / 4), std::max(1, sms / 8)};
     for (int st : strategies) {
         if (p.orth && st == GC_STRATEGY_BITMAP) continue;
