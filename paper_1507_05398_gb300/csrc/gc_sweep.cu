@@ -635,7 +635,7 @@ static Order make_order_host(const HostProblem& p) { return order_of(p, p.filter
 // Entries per resolver conflict matrix: smaller blocks build smaller
 // matrices but take more block steps.  GC_RESOLVE_BLOCK overrides (tuning).
 static uint32_t resolve_block_size() {
-    uint32_t b = 256;
+    uint32_t b = 384;
     if (const char* e = std::getenv("GC_RESOLVE_BLOCK")) b = (uint32_t)std::atoi(e);
     b = (b + 31u) & ~31u;
     return std::max<uint32_t>(32u, std::min<uint32_t>(b, kResolveBlock));
