@@ -68,3 +68,17 @@ def test_argument_errors_without_gpu():
     assert L.gc_generate64(40, 3, 4, -1, None, ctypes.byref(cnt)) == 1   # no wide B-ordering
     w = G.Problem(40, 3, 0, 4)
     assert L.gc_generate64_async(ctypes.byref(w), None, None, 0, None, None, 0, None) == 1
+
+
+def test_batch_handle_argument_errors_without_gpu():
+    L = G.lib()
+    h = ctypes.c_void_p()
+    assert L.gc_batch_create(None, 0, 0, None, 0, None, ctypes.byref(h)) == 1   # no jobs
+    assert not h.value
+    jobs = (G.Job * 1)()
+    assert L.gc_batch_create(jobs, 1, 0, None, 0, None, None) == 1              # no handle slot
+    assert L.gc_batch_launch(None, None) == 1
+    assert L.gc_batch_destroy(None) == 0
+    assert L.gc_product(None, 2, 20, None, 2, 13, None, 4, None) == 1            # 33 bits > 32
+    assert L.gc_product64(None, 0, 40, None, 0, 24, None, 0, None) == 0          # empty product
+    assert L.gc_product64(None, 0, 0, None, 0, 4, None, 0, None) == 1            # len_a = 0
