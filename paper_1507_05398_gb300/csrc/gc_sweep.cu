@@ -41,6 +41,15 @@
 namespace gc {
 
 constexpr int kChunk = 4096;       // candidates per CTA per window
+constexpr int kSlice = 128;        // distance jobs: ranks per interleaved slice
+constexpr int kMaxSlices = kChunk / kSlice;   // slices per CTA per window (32)
+constexpr int kMaxInterleaveCtas = 256;       // larger groups use contiguous chunks
+// Interleave only once the committed code is this long: below it the tests
+// are cheap and even, and the gather's fixed cost (about 3 us a window at
+// 152 CTAs) outweighs the balance it buys (measured on GB300).
+constexpr uint64_t kInterleaveMinCode = 1024;
+static_assert(kChunk <= 4096, "the interleaved gather packs segment indices in 12 bits");
+static_assert(kMaxSlices % 4 == 0 && kMaxSlices <= 32, "slice counts: one warp lane each");
 constexpr int kSurvCap = 4096;     // survivors resolved per window
 constexpr int kMaxGroupCtas = 1024;
 constexpr int kMinGroup = 8;       // CTAs of the smallest group when sizes follow cost
@@ -56,6 +65,7 @@ struct GroupDesc {
     void* store;                  // distance jobs: code beyond the shared cache
     uint64_t store_words;
     uint32_t* bitmap;             // bitmap jobs: 2^n bits, vector-indexed
+    uint8_t* slice_cnt;           // [2][ncta][kMaxSlices] survivors per slice (or null)
 };
 
 // Serving mode: jobs arrive while the kernel runs.  The host writes a job
@@ -112,6 +122,12 @@ __device__ uint32_t serve_claim(const ServeQueue& q) {
 }
 
 template <typename W>
+struct __align__(16) SweepSmem;
+// the interleaved gather's count and prefix tables live in the resolver matrix
+static_assert(kMaxSlices * kMaxInterleaveCtas * 3 <= kResolveWords * kResolveBlock * 4,
+              "gather tables must fit the resolver matrix");
+
+template <typename W>
 struct __align__(16) SweepSmem {
     uint32_t C[kMaxN + 1][kMaxN + 1];
     uint32_t pad0[3];
@@ -127,6 +143,7 @@ struct __align__(16) SweepSmem {
     uint8_t dead[kChunk];
     JobDesc job;
     GroupDesc grp;
+    uint32_t slice_cnt[kMaxSlices];  // distance jobs: survivors per local slice
     unsigned long long phase[12];  // phase timers (thread 0 of the group's first CTA)
     long long tprev;
     BlockScratch bs;
@@ -383,13 +400,35 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 }
             }
             mark_phase(0);
-            // candidates of this CTA's chunk, in rank order
+            // candidates of this CTA, in rank order.  Distance jobs deal the
+            // window out in slices of kSlice ranks, round-robin: local slice
+            // q of this CTA is slice q * G + lb of the window.  The test cost
+            // of a candidate varies by orders of magnitude along the order,
+            // and contiguous chunks left whole CTAs with the expensive ones.
+            // Bitmap jobs (cheap, even tests) and short codes keep one
+            // contiguous chunk per CTA.
+            const bool inter = job.strategy == kStratDistance && G > 1 &&
+                               G <= kMaxInterleaveCtas && grp.slice_cnt != nullptr &&
+                               K >= kInterleaveMinCode;
+            const uint64_t nslices = (span + kSlice - 1) / kSlice;
+            const uint32_t qmax =
+                inter ? (nslices > (uint64_t)lb ? (uint32_t)((nslices - lb + G - 1) / G) : 0u) : 0u;
+            const uint64_t gen_end = inter ? (uint64_t)qmax * kSlice : c1 - c0;
             uint32_t na = 0;
-            for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
-                const uint64_t r = t0 + tid;
+            for (uint64_t t0 = 0; t0 < gen_end; t0 += kBlock) {
+                uint64_t r;
+                bool in_range;
+                if (inter) {
+                    const uint64_t q = (t0 + tid) / kSlice;
+                    r = R0 + (q * G + lb) * kSlice + (t0 + tid) % kSlice;
+                    in_range = q < qmax && r < R0 + span;
+                } else {
+                    r = c0 + t0 + tid;
+                    in_range = r < c1;
+                }
                 Word x = 0;
                 bool keep = false;
-                if (r < c1) {
+                if (in_range) {
                     if constexpr (kWide) {
                         keep = unrank_wide(o, g_binom64, r, x);
                     } else {
@@ -466,7 +505,8 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             }
             mark_phase(3);
 
-            // publish this CTA's survivors and wait for the group
+            // publish this CTA's survivors (and, interleaved, how many each
+            // local slice kept) and wait for the group
             {
                 const int par = seq & 1;
                 Word* sx = seg_x + ((size_t)par * G + lb) * kChunk;
@@ -474,6 +514,16 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 for (uint32_t i = tid; i < na; i += kBlock) {
                     sx[i] = s.list_x[i];
                     so[i] = s.list_off[i];
+                }
+                if (inter) {
+                    if (tid < kMaxSlices) s.slice_cnt[tid] = 0u;
+                    __syncthreads();
+                    for (uint32_t i = tid; i < na; i += kBlock)
+                        atomicAdd(&s.slice_cnt[(s.list_off[i] / kSlice - lb) / G], 1u);
+                    __syncthreads();
+                    if (tid < kMaxSlices)
+                        grp.slice_cnt[((size_t)par * G + lb) * kMaxSlices + tid] =
+                            (uint8_t)s.slice_cnt[tid];
                 }
             }
             const int par = seq & 1;
@@ -483,17 +533,86 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             if (!ok) break;
             mark_phase(4);
 
-            // gather every CTA's survivors in CTA (= rank) order
+            // gather every CTA's survivors in rank order
             const uint32_t Suse = min(S, (uint32_t)kSurvCap);
-            for (int g = warp; g < G; g += kWarps) {
-                const uint32_t p0 = s.pref[g];
-                if (p0 >= Suse) continue;
-                const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
-                const Word* gx = seg_x + ((size_t)par * G + g) * kChunk;
-                const uint32_t* go = grp.seg_off + ((size_t)par * G + g) * kChunk;
-                for (uint32_t i = lane; i < cnt; i += 32) {
-                    s.list_x[p0 + i] = ld_cg(gx + i);
-                    s.list_off[p0 + i] = ld_cg(go + i);
+            if (!inter) {  // contiguous chunks: CTA order is rank order
+                for (int g = warp; g < G; g += kWarps) {
+                    const uint32_t p0 = s.pref[g];
+                    if (p0 >= Suse) continue;
+                    const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
+                    const Word* gx = seg_x + ((size_t)par * G + g) * kChunk;
+                    const uint32_t* go = grp.seg_off + ((size_t)par * G + g) * kChunk;
+                    for (uint32_t i = lane; i < cnt; i += 32) {
+                        s.list_x[p0 + i] = ld_cg(gx + i);
+                        s.list_off[p0 + i] = ld_cg(go + i);
+                    }
+                }
+            } else {
+                // slice (q, g) -- local slice q of CTA g -- is window slice
+                // q * G + g, so rank order is row-major order over (q, g):
+                // its survivors start at the exclusive prefix T[q][g] of the
+                // counts in that order, and sit in CTA g's segment after the
+                // survivors of its slices q' < q.  The tables reuse the
+                // resolver's matrix space (free until the resolve).
+                uint8_t* cnt8 = reinterpret_cast<uint8_t*>(&s.M[0][0]);          // [q][g]
+                uint16_t* T = reinterpret_cast<uint16_t*>(cnt8 + kMaxSlices * kMaxInterleaveCtas);
+                const uint32_t cells = (uint32_t)kMaxSlices * G;
+                // counts: CTA g published kMaxSlices bytes, read four at a time
+                for (uint32_t e = tid; e < (uint32_t)G * (kMaxSlices / 4); e += kBlock) {
+                    const uint32_t g = e / (kMaxSlices / 4), q4 = (e % (kMaxSlices / 4)) * 4;
+                    const uint32_t v = __ldcg(reinterpret_cast<const unsigned*>(
+                        grp.slice_cnt + ((size_t)par * G + g) * kMaxSlices + q4));
+#pragma unroll
+                    for (uint32_t k = 0; k < 4; ++k) cnt8[(q4 + k) * G + g] = (uint8_t)(v >> (8 * k));
+                }
+                __syncthreads();
+                // exclusive prefix in (q, g) order: each thread owns
+                // kPerThread consecutive cells
+                constexpr uint32_t kPerThread = kMaxSlices * kMaxInterleaveCtas / kBlock;
+                const uint32_t e0 = tid * kPerThread;
+                uint32_t mine = 0;
+                for (uint32_t k = 0; k < kPerThread; ++k)
+                    if (e0 + k < cells) mine += cnt8[e0 + k];
+                uint32_t tot = 0;
+                uint32_t run = block_exclusive_scan(s.bs, mine, &tot);
+                for (uint32_t k = 0; k < kPerThread; ++k)
+                    if (e0 + k < cells) {
+                        // positions past the resolver's capacity are not used
+                        T[e0 + k] = (uint16_t)min(run, 65535u);
+                        run += cnt8[e0 + k];
+                    }
+                __syncthreads();
+                // source map: one warp per source CTA g, lane q holds slice
+                // (q, g); the map entry (g << 12 | index in g's segment) of
+                // every output position goes into list_off first (shared
+                // memory only), then one pass fetches all entries at once
+                for (int g = warp; g < G; g += kWarps) {
+                    const uint32_t c = cnt8[(uint32_t)lane * G + g];
+                    uint32_t incl = c;
+#pragma unroll
+                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                        const uint32_t t = __shfl_up_sync(kFull, incl, o2);
+                        if (lane >= o2) incl += t;
+                    }
+                    const uint32_t src = incl - c;  // in CTA g's segment
+                    const uint32_t dst = T[(uint32_t)lane * G + g];
+                    unsigned any = __ballot_sync(kFull, c != 0u && dst < Suse);
+                    while (any) {
+                        const int q = __ffs(any) - 1;
+                        any &= any - 1u;
+                        const uint32_t cq = __shfl_sync(kFull, c, q);
+                        const uint32_t sq = __shfl_sync(kFull, src, q);
+                        const uint32_t dq = __shfl_sync(kFull, dst, q);
+                        for (uint32_t k = lane; k < cq && dq + k < Suse; k += 32)
+                            s.list_off[dq + k] = ((uint32_t)g << 12) | (sq + k);
+                    }
+                }
+                __syncthreads();
+                for (uint32_t pidx = tid; pidx < Suse; pidx += kBlock) {
+                    const uint32_t m = s.list_off[pidx];
+                    const uint32_t g = m >> 12, ix = m & 4095u;
+                    s.list_x[pidx] = ld_cg(seg_x + ((size_t)par * G + g) * kChunk + ix);
+                    s.list_off[pidx] = ld_cg(grp.seg_off + ((size_t)par * G + g) * kChunk + ix);
                 }
             }
             __syncthreads();
@@ -759,6 +878,7 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
     L->off_groups = off;     off += align_up(sizeof(GroupDesc) * ng);
     L->g_flags.assign(ng, 0); L->g_segx.assign(ng, 0); L->g_segoff.assign(ng, 0);
     L->g_store.assign(ng, 0); L->g_store_words.assign(ng, 0); L->g_bitmap.assign(ng, 0);
+    L->g_slice.assign(ng, 0);
     for (int g = 0; g < ng; ++g) {
         uint64_t store = 0, bits = 0;
         for (int q = L->job_begin[g]; q < L->job_end[g]; ++q) {
@@ -780,6 +900,7 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
         L->g_store[g] = off;  off += align_up(wbytes * store);
         L->g_store_words[g] = store;
         L->g_bitmap[g] = off; off += align_up((bits + 31) / 32 * 4);
+        L->g_slice[g] = off;  off += align_up((size_t)2 * G * kMaxSlices);
     }
     // ball tables, one per distinct (n, d) among bitmap jobs
     L->hball_off.assign(njobs, 0);
@@ -848,6 +969,7 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         G.store = ws + L.g_store[g];
         G.store_words = L.g_store_words[g];
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
+        G.slice_cnt = ws + L.g_slice[g];
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
@@ -1075,6 +1197,7 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
         G.store = ws + L.g_store[g];
         G.store_words = L.store_words;
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
+        G.slice_cnt = nullptr;  // serving mode: contiguous chunks
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
