@@ -23,6 +23,8 @@ struct BlockScratch {
     __align__(16) uint32_t accb[kResolveWords];
     uint32_t left[3];   // resolution rounds: "some entry still undecided"
     uint32_t flag_any;
+    uint32_t bcast[2];           // values thread 0 hands to the CTA
+    unsigned long long bcast64;
 };
 
 // ------------------------------------------------------------ compaction
@@ -94,15 +96,16 @@ __device__ __forceinline__ bool warp_scan_desc(W x, bool is_dead, const W* src,
         if (shared_dead) is_dead |= (*shared_dead != 0);
         if (__all_sync(kFull, is_dead)) break;
         uint32_t jlo;
-        if (!kGlobalSrc && (j & 31u) == 0u && j - lo >= 32u) {
-            // 32 codewords as 8 (narrow) or 16 (wide) broadcast 16-byte
-            // shared-memory loads
+        if ((j & 31u) == 0u && j - lo >= 32u) {
+            // 32 codewords as 8 (narrow) or 16 (wide) broadcast 16-byte loads
+            // (shared memory, or L2 for the global store: other SMs write it
+            // during the kernel)
             jlo = j - 32u;
             const uint4* p4 = reinterpret_cast<const uint4*>(src + jlo);
             constexpr int kVecs = 32 * (int)sizeof(W) / 16;
 #pragma unroll
             for (int q = kVecs - 1; q >= 0; --q) {
-                const uint4 c = p4[q];
+                const uint4 c = kGlobalSrc ? __ldcg(p4 + q) : p4[q];
                 bool hit;
                 if constexpr (sizeof(W) == 4) {
                     hit = (__popc(x ^ c.w) < d) | (__popc(x ^ c.z) < d) |

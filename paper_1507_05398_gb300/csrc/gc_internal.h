@@ -68,6 +68,7 @@ struct JobDesc {
     uint32_t hball_len;
     uint32_t wmin, wmax, target;
     int orth;              // self-orthogonal constraint
+    int pipelined;         // bitmap job: resolver CTA + generator CTAs
 };
 using JobDescHost = JobDesc;
 
@@ -115,7 +116,7 @@ struct BatchLayout {
     size_t smem_bytes = 0;
     std::vector<int> first_cta, ncta, job_begin, job_end, job_order;
     size_t off_err = 0, off_jobs = 0, off_order = 0, off_groups = 0;
-    std::vector<size_t> g_flags, g_segx, g_segoff, g_store, g_bitmap, g_slice, hball_off;
+    std::vector<size_t> g_flags, g_segx, g_segoff, g_store, g_bitmap, g_slice, g_pipe, hball_off;
     std::vector<uint64_t> g_store_words;
     size_t total = 0;
 };

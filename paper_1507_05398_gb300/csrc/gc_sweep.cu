@@ -66,6 +66,10 @@ struct GroupDesc {
     uint64_t store_words;
     uint32_t* bitmap;             // bitmap jobs: 2^n bits, vector-indexed
     uint8_t* slice_cnt;           // [2][ncta][kMaxSlices] survivors per slice (or null)
+    // pipelined bitmap jobs (or null): generator flags [2][ncta], then the
+    // resolver's flag; the resolver's accepts [2][kSurvCap]
+    unsigned long long* pflags;
+    uint32_t* accbuf;
 };
 
 // Serving mode: jobs arrive while the kernel runs.  The host writes a job
@@ -192,6 +196,42 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // until every CTA of the group has published seq; then s.pref holds the
 // exclusive prefix of the counts and the total is returned.  Bounded: on
 // timeout (or when another CTA reported one) sets *ok = false.
+// CTA-wide.  Waits until flags[0..nf) all carry sequence number seq (acquire
+// loads, bounded like group_exchange); then s.pref holds the exclusive prefix
+// of their counts and the total is returned.
+template <typename W>
+__device__ uint32_t await_counts(SweepSmem<W>& s, const unsigned long long* flags, int nf,
+                                 uint32_t seq, unsigned* err, long long timeout, bool* ok) {
+    uint32_t v = 0;
+    bool fine = true;
+    if ((int)threadIdx.x < nf) {
+        const long long t0 = clock64();
+        for (;;) {
+            const unsigned long long f = ld_acquire_u64(flags + threadIdx.x);
+            if ((uint32_t)(f >> 32) == seq) {
+                v = (uint32_t)f;
+                break;
+            }
+            if (ld_acquire_gpu(err) != 0u) { fine = false; break; }
+            if (clock64() - t0 > timeout) {
+                atomicExch(err, 1u);
+                fine = false;
+                break;
+            }
+        }
+    }
+    if (threadIdx.x == 0) s.bs.flag_any = 1u;
+    __syncthreads();
+    if (!fine) s.bs.flag_any = 0u;
+    uint32_t total = 0;
+    const uint32_t ex = block_exclusive_scan(s.bs, v, &total);  // has barriers
+    if ((int)threadIdx.x < nf) s.pref[threadIdx.x] = ex;
+    if (threadIdx.x == 0) s.pref[nf] = total;
+    *ok = *ok && s.bs.flag_any != 0u;
+    __syncthreads();
+    return total;
+}
+
 template <typename W>
 __device__ uint32_t group_exchange(SweepSmem<W>& s, unsigned long long* flags, int lb, int gsize,
                                    uint32_t seq, uint32_t count, unsigned* err, long long timeout,
@@ -263,6 +303,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
     const uint32_t(*C)[kMaxN + 1] = s.C;
     const bool timing = (lb == 0 && tid == 0);
     uint32_t seq = 0;
+    uint32_t pseq = 0;  // pipelined jobs: sequence numbers used so far
     bool ok = true;
     // every job's statistics start at zero (ordered before any other CTA's
     // update by the first group exchange)
@@ -353,25 +394,21 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             }
         };
 
-        while (R0 < o.N) {
-            if (timing) s.tprev = clock64();
-            const uint64_t span = min((uint64_t)W, o.N - R0);
-            const uint64_t chunk = (span + G - 1) / G;
-            const uint64_t c0 = min(R0 + (uint64_t)lb * chunk, R0 + span);
-            const uint64_t c1 = min(c0 + chunk, R0 + span);
-
-            // bitmap strategy: this CTA's share of the previous window's marks
-            if (!kWide && job.strategy == kStratBitmap && nprev > 0) {
+        // bitmap strategy: share `share` of `nshares` of the ball marks of
+        // the accepts accs[0..nacc)
+        auto mark_share = [&](const Word* accs, uint32_t nacc, int share, int nshares) {
+            if (kWide || job.strategy != kStratBitmap || nacc == 0) return;
+            {
                 const uint32_t hl = job.hball_len;
-                const uint64_t total = (uint64_t)nprev * hl;
-                const uint64_t per = (total + G - 1) / G;
-                const uint64_t q0 = min((uint64_t)lb * per, total), q1 = min(q0 + per, total);
+                const uint64_t total = (uint64_t)nacc * hl;
+                const uint64_t per = (total + nshares - 1) / nshares;
+                const uint64_t q0 = min((uint64_t)share * per, total), q1 = min(q0 + per, total);
                 // (i, j) = divmod(q, hl), advanced by kBlock without dividing
                 const uint64_t qs = q0 + tid;
                 uint32_t i = (uint32_t)(qs / hl), j = (uint32_t)(qs - (uint64_t)i * hl);
                 const uint32_t di = kBlock / hl, dj = kBlock - di * hl;
                 for (uint64_t q = qs; q < q1; q += kBlock) {
-                    const uint32_t c = (uint32_t)prev[i];
+                    const uint32_t c = (uint32_t)accs[i];
                     const uint32_t e = __ldg(job.hball + j);
                     const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
                     uint32_t mask = s.lowball[e & 7u][c & 31u];
@@ -399,6 +436,184 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     }
                 }
             }
+        };
+        // Bitmap jobs of a group of three or more CTAs run pipelined.  The
+        // group's first CTA resolves window t while the others (generators)
+        // mark the balls of window t-2's accepts and generate window t+1.
+        // When a generator generates window t, the bitmap is complete up to
+        // window t-3 (the marks of window t-3 were made during window t-1
+        // and the generators' exchange after it ordered them), so it also
+        // tests its candidates against window t-2's accepts and -- once the
+        // resolver has published them -- window t-1's.  Every CTA computes
+        // the windows by the rules of the sequential loop below, from the
+        // generators' counts.  Flags carry job-unique sequence numbers
+        // (pseq), and every wait is bounded.
+        const bool piped = !kWide && job.strategy == kStratBitmap && job.pipelined != 0 &&
+                           G >= 3 && grp.pflags != nullptr && grp.accbuf != nullptr;
+        if (piped) {
+            const int nG = G - 1, gi = lb - 1;
+            unsigned long long* gflag = grp.pflags;                  // [2][G]
+            unsigned long long* rflag = grp.pflags + 2 * (size_t)G;  // the resolver's
+            const uint32_t wmax_p = (uint32_t)min((uint64_t)job.wmax, (uint64_t)nG * kChunk);
+            W = min(W, wmax_p);
+            Word* acc_pp = s.accA;  // generators: accepts of window t-2
+            Word* acc_p = s.accB;   // generators: accepts of window t-1
+            uint32_t n_pp = 0, n_p = 0;
+            uint32_t t = 0;
+            for (; ok && R0 < o.N; ++t) {
+                if (timing) s.tprev = clock64();
+                const uint32_t wseq = pseq + t + 1;
+                const int par = t & 1;
+                const uint64_t span = min((uint64_t)W, o.N - R0);
+                if (lb > 0) {
+                    mark_share(acc_pp, n_pp, gi, nG);
+                    const uint64_t chunk = (span + nG - 1) / nG;
+                    const uint64_t c0 = min(R0 + (uint64_t)gi * chunk, R0 + span);
+                    const uint64_t c1 = min(c0 + chunk, R0 + span);
+                    uint32_t na = 0;
+                    for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
+                        const uint64_t r = t0 + tid;
+                        uint32_t x = 0;
+                        bool keep = false;
+                        if (r < c1) {
+                            keep = unrank(o, C, r, x);
+                            if (keep) keep = !((ld_cg(grp.bitmap + (x >> 5)) >> (x & 31u)) & 1u);
+                        }
+                        na = block_append(s.bs, keep, (Word)x, (uint32_t)(r - R0), s.list_x,
+                                          s.list_off, na);
+                    }
+                    na = block_filter<false>(s.bs, s.list_x, s.list_off, s.dead, na,
+                                             (const Word*)acc_pp, 0u, n_pp, d, my_tests);
+                    n_p = 0;
+                    if (t > 0) {
+                        // window t-1's accepts, once the resolver has them
+                        if (tid == 0) {
+                            const long long tw = clock64();
+                            uint32_t cnt = 0, fine = 1;
+                            for (;;) {
+                                const unsigned long long f = ld_acquire_u64(rflag);
+                                if ((uint32_t)(f >> 32) == wseq - 1) {
+                                    cnt = (uint32_t)f;
+                                    break;
+                                }
+                                if (ld_acquire_gpu(a.err) != 0u) { fine = 0; break; }
+                                if (clock64() - tw > a.timeout_cycles) {
+                                    atomicExch(a.err, 1u);
+                                    fine = 0;
+                                    break;
+                                }
+                            }
+                            s.bs.bcast[0] = cnt;
+                            s.bs.bcast[1] = fine;
+                        }
+                        __syncthreads();
+                        if (s.bs.bcast[1] == 0u) {
+                            ok = false;
+                            break;
+                        }
+                        n_p = s.bs.bcast[0];
+                        for (uint32_t i = tid; i < n_p; i += kBlock)
+                            acc_p[i] = (Word)ld_cg(grp.accbuf + (size_t)(par ^ 1) * kSurvCap + i);
+                        __syncthreads();
+                        na = block_filter<false>(s.bs, s.list_x, s.list_off, s.dead, na,
+                                                 (const Word*)acc_p, 0u, n_p, d, my_tests);
+                    }
+                    // publish this generator's survivors
+                    Word* sx = seg_x + ((size_t)par * G + gi) * kChunk;
+                    uint32_t* so = grp.seg_off + ((size_t)par * G + gi) * kChunk;
+                    for (uint32_t i = tid; i < na; i += kBlock) {
+                        sx[i] = s.list_x[i];
+                        so[i] = s.list_off[i];
+                    }
+                    __threadfence();
+                    __syncthreads();
+                    if (tid == 0)
+                        st_release_u64(gflag + (size_t)par * G + gi,
+                                       ((unsigned long long)wseq << 32) | na);
+                }
+                // every CTA: the generators' counts for window t
+                const uint32_t S = await_counts(s, gflag + (size_t)par * G, nG, wseq, a.err,
+                                                a.timeout_cycles, &ok);
+                if (!ok) break;
+                mark_phase(4);
+                const uint32_t Suse = min(S, (uint32_t)kSurvCap);
+                // the next window starts after the kSurvCap-th survivor when
+                // the window is cut (generator order is rank order)
+                if (tid == 0) {
+                    uint64_t rn = R0 + span;
+                    if (S > (uint32_t)kSurvCap) {
+                        int j = 0;
+                        while (j + 1 < nG && s.pref[j + 1] <= (uint32_t)kSurvCap - 1u) ++j;
+                        rn = R0 + ld_cg(grp.seg_off + ((size_t)par * G + j) * kChunk +
+                                        ((uint32_t)kSurvCap - 1u - s.pref[j])) + 1;
+                    }
+                    s.bs.bcast64 = rn;
+                }
+                if (lb == 0) {
+                    // the resolver: gather, resolve, commit, publish
+                    for (int g = warp; g < nG; g += kWarps) {
+                        const uint32_t p0 = s.pref[g];
+                        if (p0 >= Suse) continue;
+                        const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
+                        const Word* gx = seg_x + ((size_t)par * G + g) * kChunk;
+                        const uint32_t* go = grp.seg_off + ((size_t)par * G + g) * kChunk;
+                        for (uint32_t i = lane; i < cnt; i += 32) {
+                            s.list_x[p0 + i] = ld_cg(gx + i);
+                            s.list_off[p0 + i] = ld_cg(go + i);
+                        }
+                    }
+                    __syncthreads();
+                    mark_phase(5);
+                    uint64_t rt = 0;
+                    const uint32_t nacc =
+                        block_resolve<false>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
+                                             s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
+                                             a.resolve_block);
+                    resolve_tests += rt;
+                    mark_phase(6);
+                    for (uint32_t i = tid; i < nacc; i += kBlock) {
+                        const uint64_t pos = K + i;
+                        if (pos < job.cap) static_cast<Word*>(job.out)[pos] = cur[i];
+                        if (!o.filter && !o.even) dense += o.N - 1 - (R0 + s.acc_off[i]);
+                        grp.accbuf[(size_t)par * kSurvCap + i] = (uint32_t)cur[i];
+                    }
+                    __threadfence();
+                    __syncthreads();
+                    if (tid == 0)
+                        st_release_u64(rflag, ((unsigned long long)wseq << 32) | nacc);
+                    K += nacc;
+                    surv_total += Suse;
+                } else {
+                    __syncthreads();
+                }
+                const uint64_t Rnext = s.bs.bcast64;
+                if (S > 2u * job.target)
+                    W = max(W / 2u, job.wmin);
+                else if (S < job.target / 2u)
+                    W = min(W * 2u, wmax_p);
+                W = min(W, wmax_p);
+                R0 = Rnext;
+                ++windows;
+                if (lb > 0) {  // window t-1's accepts are window t+1's "t-2"
+                    Word* tmp = acc_pp;
+                    acc_pp = acc_p;
+                    acc_p = tmp;
+                    n_pp = n_p;
+                }
+                __syncthreads();  // bcast64 is read before thread 0 writes it again
+                mark_phase(7);
+            }
+            pseq += t + 1;
+        } else
+        while (R0 < o.N) {
+            if (timing) s.tprev = clock64();
+            const uint64_t span = min((uint64_t)W, o.N - R0);
+            const uint64_t chunk = (span + G - 1) / G;
+            const uint64_t c0 = min(R0 + (uint64_t)lb * chunk, R0 + span);
+            const uint64_t c1 = min(c0 + chunk, R0 + span);
+
+            // bitmap strategy: this CTA's share of the previous window's marks
+            mark_share(prev, nprev, lb, G);
             mark_phase(0);
             // candidates of this CTA, in rank order.  Distance jobs deal the
             // window out in slices of kSlice ranks, round-robin: local slice
@@ -879,6 +1094,7 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
     L->g_flags.assign(ng, 0); L->g_segx.assign(ng, 0); L->g_segoff.assign(ng, 0);
     L->g_store.assign(ng, 0); L->g_store_words.assign(ng, 0); L->g_bitmap.assign(ng, 0);
     L->g_slice.assign(ng, 0);
+    L->g_pipe.assign(ng, 0);
     for (int g = 0; g < ng; ++g) {
         uint64_t store = 0, bits = 0;
         for (int q = L->job_begin[g]; q < L->job_end[g]; ++q) {
@@ -901,6 +1117,13 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
         L->g_store_words[g] = store;
         L->g_bitmap[g] = off; off += align_up((bits + 31) / 32 * 4);
         L->g_slice[g] = off;  off += align_up((size_t)2 * G * kMaxSlices);
+        // pipelined bitmap jobs: flags [2G + 1] u64, then accepts [2][kSurvCap]
+        L->g_pipe[g] = 0;
+        if (bits > 0) {
+            L->g_pipe[g] = off;
+            off += align_up(sizeof(unsigned long long) * (2 * (size_t)G + 1));
+            off += align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap);
+        }
     }
     // ball tables, one per distinct (n, d) among bitmap jobs
     L->hball_off.assign(njobs, 0);
@@ -921,6 +1144,13 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
 // Host-side fault injection for tests of the failure path: GC_FAULT=wait
 // makes group 0 wait for one CTA that does not exist, with a 0.2 s limit, so
 // its bounded waits expire and every job reports GC_ERR_TIMEOUT.
+// GC_PIPELINE=0 runs bitmap jobs with the sequential window loop (for
+// measurements); pipelining is on by default.
+static bool pipeline_enabled() {
+    const char* e = std::getenv("GC_PIPELINE");
+    return !(e && std::strcmp(e, "0") == 0);
+}
+
 static bool inject_wait_fault() {
     const char* fault = std::getenv("GC_FAULT");
     return fault && std::strcmp(fault, "wait") == 0;
@@ -938,6 +1168,7 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         D.d = J.p.d;
         D.strategy = J.plan.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
         D.orth = J.p.orth ? 1 : 0;
+        D.pipelined = (D.strategy == kStratBitmap && pipeline_enabled()) ? 1 : 0;
         D.out = J.d_out;
         D.cap = J.capacity;
         D.stats = J.d_stats;
@@ -970,6 +1201,12 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         G.store_words = L.g_store_words[g];
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
         G.slice_cnt = ws + L.g_slice[g];
+        G.pflags = L.g_pipe[g] ? reinterpret_cast<unsigned long long*>(ws + L.g_pipe[g]) : nullptr;
+        G.accbuf = L.g_pipe[g]
+                       ? reinterpret_cast<uint32_t*>(
+                             ws + L.g_pipe[g] +
+                             align_up(sizeof(unsigned long long) * (2 * (size_t)L.ncta[g] + 1)))
+                       : nullptr;
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
@@ -1025,6 +1262,11 @@ int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stre
                                  sizeof(unsigned long long) * 2 * (L.ncta[g] + 1), stream)) !=
             cudaSuccess)
             return cuda_fail("group flags");
+        if (L.g_pipe[g] &&
+            (e = cudaMemsetAsync(ws + L.g_pipe[g], 0xff,
+                                 sizeof(unsigned long long) * (2 * (size_t)L.ncta[g] + 1),
+                                 stream)) != cudaSuccess)
+            return cuda_fail("pipeline flags");
     }
     const void* kernel = L.wide ? (const void*)sweep_kernel<uint64_t>
                                 : (const void*)sweep_kernel<uint32_t>;
@@ -1144,6 +1386,7 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
     D->d = p.d;
     D->strategy = pl.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
     D->orth = p.orth ? 1 : 0;
+    D->pipelined = 0;  // serving groups keep the sequential window loop
     D->out = d_out;
     D->cap = cap;
     D->stats = d_stats;
@@ -1197,7 +1440,9 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
         G.store = ws + L.g_store[g];
         G.store_words = L.store_words;
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
-        G.slice_cnt = nullptr;  // serving mode: contiguous chunks
+        G.slice_cnt = nullptr;  // serving mode: contiguous chunks, no pipeline
+        G.pflags = nullptr;
+        G.accbuf = nullptr;
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
