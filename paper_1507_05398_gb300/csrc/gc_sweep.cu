@@ -27,6 +27,12 @@
 //     Every CTA keeps its own copy of the accepts, so no second wait is needed.
 // The window size adapts so that about `target` candidates survive step 1; if
 // more than kSurvCap survive, the window is cut after the kSurvCap-th one.
+// Two refinements of this scheme:
+//  - distance jobs with a long code deal the window out in kSlice-rank
+//    slices round-robin instead of one chunk per CTA, because the test cost
+//    per candidate is very uneven along the order;
+//  - bitmap jobs on three or more CTAs run pipelined: the group's first CTA
+//    resolves window t while the others generate and filter window t+1.
 // The kernel is instantiated for narrow vectors (uint32 words, n <= 32, both
 // strategies) and wide ones (uint64 words, n <= 64, distance strategy only).
 #include <algorithm>
