@@ -167,11 +167,12 @@ uint64_t gc_capacity_bound(int n, int d, int weight_or_none);
 int gc_plan(const gc_problem *prob, gc_plan_t *out_plan);
 
 /* Measured choice: runs the candidate plans (distance or bitmap strategy,
- * survivor targets 256/512/1024/2048, all / a quarter / an eighth of the SMs) for
- * this problem on the current device, returns the fastest in *best and its
- * time in *best_ms (may be NULL), and appends it to the tuning cache if one
- * is installed.  Synchronous; allocates its own scratch.  GC_ORDER_BASIS
- * problems are tuned but not cached (the basis is not part of the key). */
+ * survivor targets 256/512/1024/2048, all / a quarter / an eighth of the
+ * SMs) for this problem (n <= 32) on the current device, returns the
+ * fastest in *best and its time in *best_ms (may be NULL), and appends it
+ * to the tuning cache if one is installed.  Synchronous; allocates its own
+ * scratch.  GC_ORDER_BASIS problems are tuned but not cached (the basis is
+ * not part of the key). */
 int gc_autotune(const gc_problem *prob, gc_plan_t *best, double *best_ms);
 
 /* Installs a plain-text tuning cache file (NULL or "" removes it; default:
