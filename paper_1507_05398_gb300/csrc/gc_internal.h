@@ -81,7 +81,7 @@ struct ServeLayout {
     uint64_t store_words = 0;      // per group
     uint64_t bitmap_bits = 0;      // per group
     size_t off_err = 0, off_head = 0, off_groups = 0, off_hball = 0, hball_bytes = 0;
-    std::vector<size_t> g_flags, g_segx, g_segoff, g_store, g_bitmap;
+    std::vector<size_t> g_flags, g_segx, g_segoff, g_store, g_bitmap, g_slice, g_pipe;
     size_t total = 0;
     // ball tables already uploaded: key (n << 8 | d) -> (offset, length)
     std::vector<std::pair<uint32_t, std::pair<size_t, uint32_t>>> hball_tables;

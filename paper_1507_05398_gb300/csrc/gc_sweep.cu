@@ -1333,6 +1333,7 @@ bool serve_layout(const gc_server_config& cfg, ServeLayout* L, std::string* why)
     L->off_groups = off; off += align_up(sizeof(GroupDesc) * ng);
     L->g_flags.assign(ng, 0); L->g_segx.assign(ng, 0); L->g_segoff.assign(ng, 0);
     L->g_store.assign(ng, 0); L->g_bitmap.assign(ng, 0);
+    L->g_slice.assign(ng, 0); L->g_pipe.assign(ng, 0);
     const int G = L->group_ctas;
     for (int g = 0; g < ng; ++g) {
         L->g_flags[g] = off;  off += align_up(sizeof(unsigned long long) * 2 * (G + 1));
@@ -1340,6 +1341,10 @@ bool serve_layout(const gc_server_config& cfg, ServeLayout* L, std::string* why)
         L->g_segoff[g] = off; off += align_up(sizeof(uint32_t) * 2 * (size_t)G * kChunk);
         L->g_store[g] = off;  off += align_up(sizeof(uint32_t) * L->store_words);
         L->g_bitmap[g] = off; off += align_up((L->bitmap_bits + 31) / 32 * 4);
+        L->g_slice[g] = off;  off += align_up((size_t)2 * G * kMaxSlices);
+        L->g_pipe[g] = off;
+        off += align_up(sizeof(unsigned long long) * (2 * (size_t)G + 1));
+        off += align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap);
     }
     L->off_hball = off;
     L->hball_bytes = 64ull << 20;
@@ -1392,7 +1397,7 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
     D->d = p.d;
     D->strategy = pl.strategy == GC_STRATEGY_BITMAP ? kStratBitmap : kStratDistance;
     D->orth = p.orth ? 1 : 0;
-    D->pipelined = 0;  // serving groups keep the sequential window loop
+    D->pipelined = (D->strategy == kStratBitmap && pipeline_enabled()) ? 1 : 0;
     D->out = d_out;
     D->cap = cap;
     D->stats = d_stats;
@@ -1446,9 +1451,10 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
         G.store = ws + L.g_store[g];
         G.store_words = L.store_words;
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
-        G.slice_cnt = nullptr;  // serving mode: contiguous chunks, no pipeline
-        G.pflags = nullptr;
-        G.accbuf = nullptr;
+        G.slice_cnt = ws + L.g_slice[g];
+        G.pflags = reinterpret_cast<unsigned long long*>(ws + L.g_pipe[g]);
+        G.accbuf = reinterpret_cast<uint32_t*>(
+            ws + L.g_pipe[g] + align_up(sizeof(unsigned long long) * (2 * (size_t)G.ncta + 1)));
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
@@ -1460,11 +1466,16 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
         return cuda_fail("group descriptors");
     if ((e = cudaMemsetAsync(ws + L.off_err, 0, 256, stream)) != cudaSuccess)
         return cuda_fail("error word");
-    for (int g = 0; g < L.ngroups; ++g)
+    for (int g = 0; g < L.ngroups; ++g) {
         if ((e = cudaMemsetAsync(ws + L.g_flags[g], 0xff,
                                  sizeof(unsigned long long) * 2 * (L.group_ctas + 1), stream)) !=
             cudaSuccess)
             return cuda_fail("group flags");
+        if ((e = cudaMemsetAsync(ws + L.g_pipe[g], 0xff,
+                                 sizeof(unsigned long long) * (2 * (size_t)L.group_ctas + 1),
+                                 stream)) != cudaSuccess)
+            return cuda_fail("pipeline flags");
+    }
     // the claim counter (zeroed when the server is created) is left as it
     // is: a relaunch continues with the first published job no group has
     // claimed
