@@ -318,7 +318,8 @@ def run_ours(args):
         "phase_ms_cta0": {f"n={n} d={d} {o}": dict(
             {ph: (c if ph in ("rounds", "blocks") else round(1e3 * c / clock_hz, 4))
              for ph, c in zip(G.Stats.PHASES, st.phase_cycles)},
-            windows=st.windows, survivors=st.survivors)
+            windows=st.windows, survivors=st.survivors, pair_windows=st.pair_windows,
+            pair_fallbacks=st.pair_fallbacks)
             for (n, d, o, w), st in zip(probs, stats_now)},
         "e2e": {"value": e2e_value, "unit": "tests/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h,

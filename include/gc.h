@@ -127,14 +127,22 @@ typedef struct {
     uint64_t survivors;        /* candidates that reached the resolver */
     int32_t status;            /* GC_OK or GC_ERR_TIMEOUT / _INTERNAL */
     int32_t strategy;          /* strategy that ran */
-    /* Diagnostic: SM cycles the first CTA of the job's group spent, summed
-     * over windows, in [0] ball marking, [1] candidate generation and bitmap
-     * lookup, [2] the newest-codeword test and compaction, [3] the split test
-     * against older codewords, [4] publishing and waiting for the group,
-     * [5] gathering survivors, [6] resolving, [7] committing; within [6]:
-     * [8] conflict matrix, [9] resolution rounds, [10] appending and the
-     * kill step; [11] counts resolution rounds (not cycles). */
+    /* Diagnostic: SM cycles the first CTA of the job's group (or CTA
+     * GC_TIMING_CTA of it) spent, summed over windows, in [0] ball marking,
+     * [1] candidate generation and bitmap lookup, [2] the newest-codeword
+     * test and compaction, [3] the split test against older codewords,
+     * [4] publishing and waiting for the group, [5] gathering survivors,
+     * [6] resolving (a pipelined job's generator CTAs: searching the window's
+     * conflicting pairs), [7] committing; within [6]: [8] conflict matrix or
+     * bucketed search, [9] resolution rounds, [10] appending and the kill
+     * step; [11] counts resolution rounds (not cycles). */
     uint64_t phase_cycles[12];
+    /* Pipelined bitmap jobs in large groups: windows decided from the list
+     * of their conflicting pairs that the group's generator CTAs found, and
+     * windows where that list overflowed, so the conflict matrices decided
+     * them. */
+    uint64_t pair_windows;
+    uint64_t pair_fallbacks;
 } gc_stats;
 
 /* ---- information ------------------------------------------------------ */
@@ -391,8 +399,10 @@ int gc_block_test(int d, const uint32_t *d_cand, uint64_t ncand,
 /* Step 3, in-order resolve (Section 4 restricted to a list): given
  * candidates already known to clear every earlier codeword, accept them in
  * list order exactly as the serial sweep would: d_accepted[k] = list index of
- * the k-th accepted candidate, *d_count = number accepted.  ncand <= 65536.
- * Device pointers. */
+ * the k-th accepted candidate, *d_count = number accepted.  ncand <= 4096
+ * (GC_ERR_INVALID above).  Lists with few conflicts go through the bucketed
+ * resolver, the rest through conflict matrices; both give the serial result
+ * (GC_SPARSE=0 in the environment forces the matrices).  Device pointers. */
 int gc_resolve(int d, const uint32_t *d_cand, uint32_t ncand,
                uint32_t *d_accepted, uint32_t *d_count, void *stream);
 

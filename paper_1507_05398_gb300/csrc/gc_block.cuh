@@ -25,6 +25,10 @@ struct BlockScratch {
     uint32_t flag_any;
     uint32_t bcast[2];           // values thread 0 hands to the CTA
     unsigned long long bcast64;
+    uint32_t sp_masks[8];        // sparse resolver: bit blocks of the varying bits
+    uint32_t sp_vary;            // sparse resolver: bits that vary over the list
+    uint32_t sp_pairs;           // sparse resolver: pairs the buckets hold
+    uint32_t sp_edges;           // sparse resolver: conflicts found
 };
 
 // ------------------------------------------------------------ compaction
@@ -58,6 +62,37 @@ __device__ __forceinline__ uint32_t block_append(BlockScratch& bs, bool keep, W 
     const uint32_t total = bs.warp_sum[kWarps];
     __syncthreads();
     return base + total;
+}
+
+// CTA-wide.  Exclusive prefix over the CTA of one value per thread; total
+// in *total.  Ends with a barrier, so bs may be reused at once.
+__device__ __forceinline__ uint32_t block_exclusive_scan(BlockScratch& bs, uint32_t v,
+                                                         uint32_t* total) {
+    const int lane = lane_id(), warp = warp_id();
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) bs.warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < kWarps ? bs.warp_sum[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < kWarps) bs.warp_sum[lane] = wi - w;
+        if (lane == 31) bs.warp_sum[kWarps] = wi;
+    }
+    __syncthreads();
+    const uint32_t ex = bs.warp_sum[warp] + incl - v;
+    *total = bs.warp_sum[kWarps];
+    __syncthreads();
+    return ex;
 }
 
 // CTA-wide.  Keeps the entries of x/off[0..n) whose dead flag is 0, in
@@ -350,6 +385,217 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
         tick(2);
     }
     return nacc;
+}
+
+// ------------------------------------------------------------ pair resolver
+// CTA-wide, narrow words.  Decides the list x[0..n) (n <= 4096) in order,
+// as the serial greedy would (Section 4), from the list of its conflicting
+// pairs: pairs[e] = (k << 16) | i for entries k < i within distance d-1 (or
+// otherwise in conflict); every conflicting pair must be listed, duplicates
+// are harmless.  Rounds: an undecided entry with an accepted earlier
+// neighbour is rejected, one whose earlier neighbours are all rejected is
+// accepted; the first undecided entry always decides, so the rounds end, and
+// every decision rests on final ones.  Accepted entries are appended in
+// order to acc/acc_off (off may be null when acc_off is).  Returns how many.
+//   state  n bytes, flags 2 * 4096 bytes of scratch
+// tim (optional, thread 0): cycles to tim[1] rounds and tim[2] append,
+// tim[3] counts rounds.
+__device__ __forceinline__ uint32_t pair_resolve(BlockScratch& bs, const uint32_t* x,
+                                                 const uint32_t* off, uint8_t* state, uint32_t n,
+                                                 const uint32_t* pairs, uint32_t np,
+                                                 uint8_t* flags, uint32_t* acc, uint32_t* acc_off,
+                                                 unsigned long long* tim = nullptr) {
+    const int lane = lane_id();
+    const bool timing = tim && threadIdx.x == 0;
+    long long t_last = timing ? clock64() : 0;
+    uint8_t* killed = flags;           // an accepted earlier neighbour seen this round
+    uint8_t* blocked = flags + 4096;   // an undecided earlier neighbour seen this round
+    for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
+        state[i] = 0;  // 0 undecided, 1 accepted, 2 rejected
+        killed[i] = 0;
+        blocked[i] = 0;
+    }
+    if (threadIdx.x < 3) bs.left[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t round = 0;; ++round) {
+        if (timing) tim[3] += 1;
+        // this round's flag slot; the next one was last read two rounds ago
+        const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
+        if (threadIdx.x == 0) bs.left[next] = 0u;
+        for (uint32_t e = threadIdx.x; e < np; e += kBlock) {
+            const uint32_t k = pairs[e] >> 16, i = pairs[e] & 0xffffu;
+            if (state[i] == 0) {
+                const uint8_t sk = state[k];
+                if (sk == 1) killed[i] = 1;
+                else if (sk == 0) blocked[i] = 1;
+            }
+        }
+        __syncthreads();
+        // decide, and clear the marks for the next round (the thread that
+        // reads an entry's marks is the one that clears them)
+        bool left = false;
+        for (uint32_t i = threadIdx.x; i < n; i += kBlock)
+            if (state[i] == 0) {
+                if (killed[i]) state[i] = 2;
+                else if (!blocked[i]) state[i] = 1;
+                else left = true;
+                killed[i] = 0;
+                blocked[i] = 0;
+            }
+        if (__any_sync(kFull, left) && lane == 0) bs.left[slot] = 1u;
+        __syncthreads();
+        if (bs.left[slot] == 0u) break;
+    }
+    if (timing) {
+        const long long t = clock64();
+        tim[1] += (unsigned long long)(t - t_last);
+        t_last = t;
+    }
+    uint32_t nacc = 0;
+    for (uint32_t t0 = 0; t0 < n; t0 += kBlock) {
+        const uint32_t i = t0 + threadIdx.x;
+        const bool keep = i < n && state[i] == 1;
+        nacc = block_append(bs, keep, keep ? x[i] : 0u, (keep && acc_off) ? off[i] : 0u, acc,
+                            acc_off, nacc);
+    }
+    if (timing) tim[2] += (unsigned long long)(clock64() - t_last);
+    return nacc;
+}
+
+// ------------------------------------------------------------ sparse resolver
+// CTA-wide, narrow words, no orthogonality constraint.  The same decisions as
+// block_resolve, through bucketed conflict detection, for lists whose
+// conflicts are few.  Two words within distance d-1 differ in at most d-1 of
+// the bits that vary over the list; split those bits into d blocks and the
+// two words agree on at least one of them (pigeonhole), so only pairs that
+// share a block's value -- hashed into kSpBuckets buckets -- are tested.  The
+// greedy then runs in rounds over the conflicting pairs: an entry is
+// rejected once an earlier neighbour is accepted and accepted once every
+// earlier neighbour is rejected (the first undecided entry always decides).
+// Returns false, having written nothing, when d is out of range, the buckets
+// hold more than pair_budget pairs or the conflicts overflow the scratch;
+// the caller then runs block_resolve.
+//   x/off[0..n)   candidates in order (n <= 4096; not modified)
+//   state         n bytes of scratch
+//   acc/acc_off   receives accepted vectors/offsets in order (acc, n words,
+//                 is scratch until then)
+//   scratch       8192 words of shared memory (the resolver matrix)
+// tim as for block_resolve: [0] bucketed search, [1] rounds, [2] append.
+constexpr uint32_t kSpBuckets = 1024;
+constexpr uint32_t kSpEdges = 4096;
+static_assert(kSpBuckets == (uint32_t)kBlock, "one bucket per thread in the scan");
+
+__device__ __forceinline__ uint32_t sp_hash(uint32_t v) { return (v * 0x9E3779B1u) >> 22; }
+
+__device__ __forceinline__ bool sparse_resolve(BlockScratch& bs, const uint32_t* x,
+                                               const uint32_t* off, uint8_t* state, uint32_t n,
+                                               int d, uint32_t* acc, uint32_t* acc_off,
+                                               uint32_t* scratch, uint32_t pair_budget,
+                                               uint64_t& nt, uint32_t* nacc_out,
+                                               unsigned long long* tim = nullptr) {
+    if (d < 2 || d > 8 || n < 2 || n > 4096) return false;
+    const bool timing = tim && threadIdx.x == 0;
+    long long t_last = timing ? clock64() : 0;
+    auto tick = [&](int k) {
+        if (timing) {
+            const long long t = clock64();
+            tim[k] += (unsigned long long)(t - t_last);
+            t_last = t;
+        }
+    };
+    uint32_t* cnt = scratch;                                            // [kSpBuckets]
+    uint32_t* fill = scratch + kSpBuckets;                              // [kSpBuckets]
+    uint16_t* order = reinterpret_cast<uint16_t*>(scratch + 2 * kSpBuckets);  // [n]
+    uint32_t* edges = scratch + 4096;                                   // [kSpEdges]
+    const int lane = lane_id();
+    // the bits that vary over the list
+    uint32_t v = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += kBlock) v |= x[i] ^ x[0];
+    for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
+    if (threadIdx.x == 0) {
+        bs.sp_vary = 0u;
+        bs.sp_pairs = 0u;
+        bs.sp_edges = 0u;
+    }
+    __syncthreads();
+    if (lane == 0 && v) atomicOr(&bs.sp_vary, v);
+    __syncthreads();
+    const uint32_t vary = bs.sp_vary;
+    const int nv = __popc(vary);
+    if (nv < d) return false;  // every pair would be tested
+    if (threadIdx.x == 0) {
+        // block b takes the varying bits of ranks [b nv / d, (b+1) nv / d)
+        uint32_t rest = vary;
+        int r = 0;
+        for (int b = 0; b < 8; ++b) bs.sp_masks[b] = 0u;
+        while (rest) {
+            const uint32_t bit = rest & (0u - rest);
+            rest ^= bit;
+            bs.sp_masks[(r * d) / nv] |= bit;
+            ++r;
+        }
+    }
+    __syncthreads();
+    uint64_t tests = 0;
+    for (int b = 0; b < d; ++b) {
+        const uint32_t mask = bs.sp_masks[b];
+        for (uint32_t h = threadIdx.x; h < kSpBuckets; h += kBlock) cnt[h] = 0u;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += kBlock) atomicAdd(&cnt[sp_hash(x[i] & mask)], 1u);
+        __syncthreads();
+        // pairs this blocking would test; give up when they cost too much
+        uint32_t pairs = 0;
+        for (uint32_t h = threadIdx.x; h < kSpBuckets; h += kBlock)
+            pairs += cnt[h] * (cnt[h] - (cnt[h] ? 1u : 0u)) / 2u;
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
+        if (lane == 0 && pairs) atomicAdd(&bs.sp_pairs, pairs);
+        uint32_t total = 0;
+        const uint32_t h0 = threadIdx.x;  // one bucket per thread (kSpBuckets == kBlock)
+        const uint32_t start = block_exclusive_scan(bs, h0 < kSpBuckets ? cnt[h0] : 0u, &total);
+        if (bs.sp_pairs > pair_budget) return false;  // uniform: read after the scan's barriers
+        if (h0 < kSpBuckets) fill[h0] = start;
+        __syncthreads();
+        // bucket order: index in order[], vector in acc[] (free until the
+        // accepts are appended)
+        for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
+            const uint32_t p = atomicAdd(&fill[sp_hash(x[i] & mask)], 1u);
+            order[p] = (uint16_t)i;
+            acc[p] = x[i];
+        }
+        __syncthreads();
+        // every pair of a bucket, tested once from its later entry; fill[h]
+        // is now the end of bucket h and cnt[h] its size.  Threads stop once
+        // the conflicts overflow the scratch.
+        const volatile uint32_t* found = &bs.sp_edges;
+        for (uint32_t p = threadIdx.x; p < n && *found <= kSpEdges; p += kBlock) {
+            const uint32_t i = order[p];
+            const uint32_t xi = acc[p];
+            const uint32_t h = sp_hash(xi & mask);
+            const uint32_t e1 = fill[h], e0 = e1 - cnt[h];
+            for (uint32_t q = e0; q < e1; ++q) {
+                const uint32_t k = order[q];
+                const uint32_t xk = acc[q];
+                if (k >= i) continue;
+                ++tests;
+                if (__popc(xi ^ xk) < d) {
+                    const uint32_t e = atomicAdd(&bs.sp_edges, 1u);
+                    if (e < kSpEdges) edges[e] = (k << 16) | i;
+                }
+            }
+        }
+        __syncthreads();
+        if (bs.sp_edges > kSpEdges) {
+            nt += tests;
+            return false;  // uniform: read after the barrier
+        }
+    }
+    nt += tests;
+    const uint32_t ne = bs.sp_edges;
+    if (ne > kSpEdges) return false;
+    uint8_t* killed = reinterpret_cast<uint8_t*>(scratch + 2 * kSpBuckets);  // [n]
+    tick(0);
+    *nacc_out = pair_resolve(bs, x, off, state, n, edges, ne, killed, acc, acc_off, tim);
+    return true;
 }
 
 }  // namespace gc

@@ -232,6 +232,8 @@ __global__ void all_accepted_stats(gc_stats* st, uint64_t N, int strategy) {
     st->status = 0;
     st->strategy = strategy;
     for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
+    st->pair_windows = 0;
+    st->pair_fallbacks = 0;
 }
 
 // wide: run the uint64-word kernel (n <= 64; d_out holds uint64 words).

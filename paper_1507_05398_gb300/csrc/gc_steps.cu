@@ -3,6 +3,8 @@
 // They share the device primitives of the persistent sweep (gc_block.cuh),
 // so a test of a step exercises the code the sweep runs.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "gc_block.cuh"
 #include "gc_internal.h"
@@ -134,7 +136,7 @@ int launch_block_test(int d, const uint32_t* d_cand, uint64_t ncand, const uint3
 // ---------------------------------------------------------------- resolve
 __global__ void __launch_bounds__(kBlock, 1)
     resolve_kernel(int d, const uint32_t* cand, uint32_t ncand, uint32_t* acc_idx,
-                   uint32_t* count) {
+                   uint32_t* count, int sparse) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     StepSmem& s = *reinterpret_cast<StepSmem*>(smem_raw);
     for (uint32_t i = threadIdx.x; i < ncand; i += kBlock) {
@@ -143,7 +145,12 @@ __global__ void __launch_bounds__(kBlock, 1)
     }
     __syncthreads();
     uint64_t nt = 0;
-    const uint32_t na = block_resolve(s.bs, s.x, s.off, s.dead, ncand, d, s.acc, s.tile, s.M, nt);
+    // the bucketed resolver first (it gives up on lists with many
+    // conflicts), then the conflict-matrix resolver
+    uint32_t na = 0;
+    const bool done = sparse && sparse_resolve(s.bs, s.x, s.off, s.dead, ncand, d, s.acc, s.tile,
+                                               &s.M[0][0], (ncand * ncand) >> 3, nt, &na);
+    if (!done) na = block_resolve(s.bs, s.x, s.off, s.dead, ncand, d, s.acc, s.tile, s.M, nt);
     for (uint32_t i = threadIdx.x; i < na; i += kBlock) acc_idx[i] = s.tile[i];
     if (threadIdx.x == 0) *count = na;
 }
@@ -155,7 +162,9 @@ int launch_resolve(int d, const uint32_t* d_cand, uint32_t ncand, uint32_t* d_ac
     cudaError_t e = cudaFuncSetAttribute(resolve_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(GC_ERR_CUDA, cudaGetErrorString(e));
-    resolve_kernel<<<1, kBlock, smem, st>>>(d, d_cand, ncand, d_acc, d_count);
+    const char* env = std::getenv("GC_SPARSE");
+    const int sparse = (env && std::strcmp(env, "0") == 0) ? 0 : 1;
+    resolve_kernel<<<1, kBlock, smem, st>>>(d, d_cand, ncand, d_acc, d_count, sparse);
     return check_launch("resolve");
 }
 

@@ -57,6 +57,16 @@ constexpr uint64_t kInterleaveMinCode = 1024;
 static_assert(kChunk <= 4096, "the interleaved gather packs segment indices in 12 bits");
 static_assert(kMaxSlices % 4 == 0 && kMaxSlices <= 32, "slice counts: one warp lane each");
 constexpr int kSurvCap = 4096;     // survivors resolved per window
+// Pipelined windows: conflicting pairs one generator may publish, and pairs
+// the resolver takes into shared memory (behind 8 KiB of round flags in the
+// resolver matrix); more and the window goes to the conflict matrices.
+constexpr uint32_t kPairCap = 2048;
+constexpr uint32_t kPairShared = 6144;
+// Generators list the conflicts only in groups with at least this many of
+// them: in smaller groups the generators' own work per window already
+// paces the pipeline, and the search lengthens it by more than the
+// resolver saves (measured on the n = 20, d = 4 codes in groups of ~30).
+constexpr int kPairMinGenerators = 64;
 constexpr int kMaxGroupCtas = 1024;
 constexpr int kMinGroup = 8;       // CTAs of the smallest group when sizes follow cost
 enum : int { kStratDistance = 1, kStratBitmap = 2 };
@@ -72,10 +82,13 @@ struct GroupDesc {
     uint64_t store_words;
     uint32_t* bitmap;             // bitmap jobs: 2^n bits, vector-indexed
     uint8_t* slice_cnt;           // [2][ncta][kMaxSlices] survivors per slice (or null)
-    // pipelined bitmap jobs (or null): generator flags [2][ncta], then the
-    // resolver's flag; the resolver's accepts [2][kSurvCap]
+    // pipelined bitmap jobs (or null): generator survivor flags [2][ncta],
+    // the resolver's flag, generator pair flags [2][ncta]; the resolver's
+    // accepts [2][kSurvCap]; the generators' conflicting pairs
+    // [2][ncta][kPairCap]
     unsigned long long* pflags;
     uint32_t* accbuf;
+    uint32_t* pairbuf;
 };
 
 // Serving mode: jobs arrive while the kernel runs.  The host writes a job
@@ -101,6 +114,8 @@ struct BatchArgs {
     uint32_t cache_words;
     long long timeout_cycles;
     uint32_t resolve_block;       // entries per conflict matrix (<= kResolveBlock)
+    uint32_t pairs;               // 1: pipelined generators list each window's conflicts
+    uint32_t timing_cta;          // CTA of each group whose phases are timed
     ServeQueue queue;             // used when queue.descs != nullptr
 };
 
@@ -158,36 +173,6 @@ struct __align__(16) SweepSmem {
     long long tprev;
     BlockScratch bs;
 };
-
-// Exclusive prefix over the CTA of one value per thread; total in *total.
-__device__ __forceinline__ uint32_t block_exclusive_scan(BlockScratch& bs, uint32_t v,
-                                                         uint32_t* total) {
-    const int lane = lane_id(), warp = warp_id();
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) bs.warp_sum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < kWarps ? bs.warp_sum[lane] : 0u;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < kWarps) bs.warp_sum[lane] = wi - w;
-        if (lane == 31) bs.warp_sum[kWarps] = wi;
-    }
-    __syncthreads();
-    const uint32_t ex = bs.warp_sum[warp] + incl - v;
-    *total = bs.warp_sum[kWarps];
-    __syncthreads();
-    return ex;
-}
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -307,7 +292,10 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
     const int lb = (int)blockIdx.x - grp.first_cta;
     const int G = grp.ncta;
     const uint32_t(*C)[kMaxN + 1] = s.C;
-    const bool timing = (lb == 0 && tid == 0);
+    // phase timers: thread 0 of one CTA of the group (the first, unless the
+    // launch names another)
+    const bool timing = (lb == (a.timing_cta < (uint32_t)grp.ncta ? (int)a.timing_cta : 0) &&
+                         tid == 0);
     uint32_t seq = 0;
     uint32_t pseq = 0;  // pipelined jobs: sequence numbers used so far
     bool ok = true;
@@ -319,6 +307,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             st->codewords = 0; st->candidates = 0; st->dense_tests = 0; st->executed_tests = 0;
             st->marks = 0; st->windows = 0; st->survivors = 0; st->status = 0; st->strategy = 0;
             for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
+            st->pair_windows = 0; st->pair_fallbacks = 0;
         }
 
     const bool serving = a.queue.descs != nullptr;
@@ -349,6 +338,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             st->codewords = 0; st->candidates = 0; st->dense_tests = 0; st->executed_tests = 0;
             st->marks = 0; st->windows = 0; st->survivors = 0; st->status = 0; st->strategy = 0;
             for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
+            st->pair_windows = 0; st->pair_fallbacks = 0;
         }
         const JobDesc& job = s.job;
         const Order& o = job.ord;
@@ -398,6 +388,17 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 s.phase[k] += (unsigned long long)(t - s.tprev);
                 s.tprev = t;
             }
+        };
+        // resolves the gathered window in order with conflict matrices
+        uint64_t pair_done = 0, pair_failed = 0;  // windows decided from pair lists
+        auto resolve = [&](uint32_t Suse, uint64_t& rt) -> uint32_t {
+            return job.orth ? block_resolve<true>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
+                                                  s.acc_off, s.M, rt,
+                                                  timing ? s.phase + 8 : nullptr, a.resolve_block)
+                            : block_resolve<false>(s.bs, s.list_x, s.list_off, s.dead, Suse, d,
+                                                   cur, s.acc_off, s.M, rt,
+                                                   timing ? s.phase + 8 : nullptr,
+                                                   a.resolve_block);
         };
 
         // bitmap strategy: share `share` of `nshares` of the ball marks of
@@ -460,11 +461,16 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             const int nG = G - 1, gi = lb - 1;
             unsigned long long* gflag = grp.pflags;                  // [2][G]
             unsigned long long* rflag = grp.pflags + 2 * (size_t)G;  // the resolver's
+            unsigned long long* eflag = rflag + 1;                   // [2][G] pair counts
             const uint32_t wmax_p = (uint32_t)min((uint64_t)job.wmax, (uint64_t)nG * kChunk);
             W = min(W, wmax_p);
             Word* acc_pp = s.accA;  // generators: accepts of window t-2
             Word* acc_p = s.accB;   // generators: accepts of window t-1
             uint32_t n_pp = 0, n_p = 0;
+            // whether window t's conflicts are listed as pairs: the resolver
+            // decides it at the end of window t-1 (mostly accepted: few
+            // conflicts) and hands it to the generators in its flag
+            bool pairs_on = false;
             uint32_t t = 0;
             for (; ok && R0 < o.N; ++t) {
                 if (timing) s.tprev = clock64();
@@ -473,6 +479,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                 const uint64_t span = min((uint64_t)W, o.N - R0);
                 if (lb > 0) {
                     mark_share(acc_pp, n_pp, gi, nG);
+                    mark_phase(0);
                     const uint64_t chunk = (span + nG - 1) / nG;
                     const uint64_t c0 = min(R0 + (uint64_t)gi * chunk, R0 + span);
                     const uint64_t c1 = min(c0 + chunk, R0 + span);
@@ -488,8 +495,10 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                         na = block_append(s.bs, keep, (Word)x, (uint32_t)(r - R0), s.list_x,
                                           s.list_off, na);
                     }
+                    mark_phase(1);
                     na = block_filter<false>(s.bs, s.list_x, s.list_off, s.dead, na,
                                              (const Word*)acc_pp, 0u, n_pp, d, my_tests);
+                    mark_phase(2);
                     n_p = 0;
                     if (t > 0) {
                         // window t-1's accepts, once the resolver has them
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                             for (;;) {
                                 const unsigned long long f = ld_acquire_u64(rflag);
                                 if ((uint32_t)(f >> 32) == wseq - 1) {
-                                    cnt = (uint32_t)f;
+                                    cnt = (uint32_t)f;  // bit 31: pairs for window t
                                     break;
                                 }
                                 if (ld_acquire_gpu(a.err) != 0u) { fine = 0; break; }
@@ -517,12 +526,15 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                             ok = false;
                             break;
                         }
-                        n_p = s.bs.bcast[0];
+                        n_p = s.bs.bcast[0] & 0x7fffffffu;
+                        pairs_on = (s.bs.bcast[0] >> 31) != 0u;
+                        mark_phase(4);
                         for (uint32_t i = tid; i < n_p; i += kBlock)
                             acc_p[i] = (Word)ld_cg(grp.accbuf + (size_t)(par ^ 1) * kSurvCap + i);
                         __syncthreads();
                         na = block_filter<false>(s.bs, s.list_x, s.list_off, s.dead, na,
                                                  (const Word*)acc_p, 0u, n_p, d, my_tests);
+                        mark_phase(3);
                     }
                     // publish this generator's survivors
                     Word* sx = seg_x + ((size_t)par * G + gi) * kChunk;
@@ -555,6 +567,45 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     }
                     s.bs.bcast64 = rn;
                 }
+                // The generators list the window's conflicting pairs: each
+                // gathers the window and tests entry i against every earlier
+                // entry for i = gi (mod nG), and publishes what it found.
+                // The resolver then only runs the decision rounds (or, when
+                // the pairs overflow, its own conflict matrices).
+                const bool by_pairs = pairs_on && Suse >= 2u;
+                if (lb > 0 && by_pairs) {
+                    for (int g = warp; g < nG; g += kWarps) {
+                        const uint32_t p0 = s.pref[g];
+                        if (p0 >= Suse) continue;
+                        const uint32_t cnt = min(s.pref[g + 1] - p0, Suse - p0);
+                        const Word* gx = seg_x + ((size_t)par * G + g) * kChunk;
+                        for (uint32_t i = lane; i < cnt; i += 32) s.list_x[p0 + i] = ld_cg(gx + i);
+                    }
+                    if (tid == 0) s.bs.sp_edges = 0u;
+                    __syncthreads();
+                    mark_phase(5);
+                    uint32_t* pb = grp.pairbuf + ((size_t)par * G + gi) * kPairCap;
+                    volatile uint32_t* found = &s.bs.sp_edges;
+                    for (uint32_t i = (uint32_t)gi; i < Suse && *found <= kPairCap; i += nG) {
+                        const Word xi = s.list_x[i];
+                        for (uint32_t k = tid; k < i; k += kBlock) {
+                            ++my_tests;
+                            if (popc(xi ^ s.list_x[k]) < d) {
+                                const uint32_t e = atomicAdd(&s.bs.sp_edges, 1u);
+                                if (e < kPairCap) pb[e] = (k << 16) | i;
+                            }
+                        }
+                    }
+                    __threadfence();
+                    __syncthreads();
+                    if (tid == 0) {
+                        const uint32_t np = s.bs.sp_edges;
+                        st_release_u64(eflag + (size_t)par * G + gi,
+                                       ((unsigned long long)wseq << 32) |
+                                           (np > kPairCap ? kPairShared + 1u : np));
+                    }
+                    mark_phase(6);
+                }
                 if (lb == 0) {
                     // the resolver: gather, resolve, commit, publish
                     for (int g = warp; g < nG; g += kWarps) {
@@ -571,10 +622,33 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     __syncthreads();
                     mark_phase(5);
                     uint64_t rt = 0;
-                    const uint32_t nacc =
-                        block_resolve<false>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                             s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
-                                             a.resolve_block);
+                    uint32_t nacc = 0;
+                    bool decided = false;
+                    if (by_pairs) {
+                        const uint32_t np = await_counts(s, eflag + (size_t)par * G, nG, wseq,
+                                                         a.err, a.timeout_cycles, &ok);
+                        if (!ok) break;
+                        mark_phase(4);
+                        if (np <= kPairShared) {
+                            uint32_t* pr = &s.M[0][0] + 2048;  // after 8 KiB of round flags
+                            for (int g = warp; g < nG; g += kWarps) {
+                                const uint32_t p0 = s.pref[g], c = s.pref[g + 1] - p0;
+                                const uint32_t* src = grp.pairbuf + ((size_t)par * G + g) * kPairCap;
+                                for (uint32_t i = lane; i < c; i += 32) pr[p0 + i] = ld_cg(src + i);
+                            }
+                            __syncthreads();
+                            if constexpr (!kWide)  // pipelining is for narrow words
+                                nacc = pair_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, pr,
+                                                    np, reinterpret_cast<uint8_t*>(&s.M[0][0]),
+                                                    cur, s.acc_off,
+                                                    timing ? s.phase + 8 : nullptr);
+                            decided = true;
+                            ++pair_done;
+                        } else {
+                            ++pair_failed;
+                        }
+                    }
+                    if (!decided) nacc = resolve(Suse, rt);
                     resolve_tests += rt;
                     mark_phase(6);
                     for (uint32_t i = tid; i < nacc; i += kBlock) {
@@ -585,8 +659,11 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     }
                     __threadfence();
                     __syncthreads();
+                    pairs_on = a.pairs != 0u && nG >= kPairMinGenerators &&
+                               8u * (Suse - nacc) <= Suse;
                     if (tid == 0)
-                        st_release_u64(rflag, ((unsigned long long)wseq << 32) | nacc);
+                        st_release_u64(rflag, ((unsigned long long)wseq << 32) |
+                                                  (pairs_on ? 0x80000000ull : 0ull) | nacc);
                     K += nacc;
                     surv_total += Suse;
                 } else {
@@ -843,13 +920,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
 
             // resolve in order; identical in every CTA of the group
             uint64_t rt = 0;
-            const uint32_t nacc =
-                job.orth ? block_resolve<true>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                               s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
-                                               a.resolve_block)
-                         : block_resolve<false>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
-                                                s.acc_off, s.M, rt, timing ? s.phase + 8 : nullptr,
-                                                a.resolve_block);
+            const uint32_t nacc = resolve(Suse, rt);
             if (lb == 0) resolve_tests += rt;
             mark_phase(6);
 
@@ -904,8 +975,11 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             job.stats->windows = windows;
             job.stats->survivors = surv_total;
             job.stats->strategy = job.strategy;
-            for (int k = 0; k < 12; ++k) job.stats->phase_cycles[k] = s.phase[k];
+            job.stats->pair_windows = pair_done;
+            job.stats->pair_fallbacks = pair_failed;
         }
+        if (timing)
+            for (int k = 0; k < 12; ++k) job.stats->phase_cycles[k] = s.phase[k];
         // the next job reuses the statistics-free scratch; make sure every CTA
         // of the group is done with this job's shared state first
         __syncthreads();
@@ -969,6 +1043,22 @@ uint64_t high_ball_len(int n, int d) {
 
 // ------------------------------------------------------------------ host side
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Pipelined bitmap jobs, per group of G CTAs: flags [4G + 1] u64, the
+// accepts [2][kSurvCap] u32, the conflicting pairs [2][G][kPairCap] u32.
+static size_t pipe_flag_bytes(int G) {
+    return align_up(sizeof(unsigned long long) * (4 * (size_t)G + 1));
+}
+static size_t pipe_bytes(int G) {
+    return pipe_flag_bytes(G) + align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap) +
+           align_up(sizeof(uint32_t) * 2 * (size_t)G * kPairCap);
+}
+static void set_pipe(GroupDesc& D, uint8_t* base) {
+    D.pflags = reinterpret_cast<unsigned long long*>(base);
+    D.accbuf = reinterpret_cast<uint32_t*>(base + pipe_flag_bytes(D.ncta));
+    D.pairbuf = reinterpret_cast<uint32_t*>(base + pipe_flag_bytes(D.ncta) +
+                                            align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap));
+}
 
 static Order make_order_host(const HostProblem& p) { return order_of(p, p.filter, p.orth); }
 
@@ -1123,12 +1213,11 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
         L->g_store_words[g] = store;
         L->g_bitmap[g] = off; off += align_up((bits + 31) / 32 * 4);
         L->g_slice[g] = off;  off += align_up((size_t)2 * G * kMaxSlices);
-        // pipelined bitmap jobs: flags [2G + 1] u64, then accepts [2][kSurvCap]
+        // pipelined bitmap jobs (sized, like the flags, for one spare CTA)
         L->g_pipe[g] = 0;
         if (bits > 0) {
             L->g_pipe[g] = off;
-            off += align_up(sizeof(unsigned long long) * (2 * (size_t)G + 1));
-            off += align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap);
+            off += pipe_bytes(G + 1);
         }
     }
     // ball tables, one per distinct (n, d) among bitmap jobs
@@ -1152,6 +1241,20 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
 // its bounded waits expire and every job reports GC_ERR_TIMEOUT.
 // GC_PIPELINE=0 runs bitmap jobs with the sequential window loop (for
 // measurements); pipelining is on by default.
+// Pipelined windows: the generators list the window's conflicting pairs for
+// the resolver; GC_PAIRS=0 turns it off (measurements).
+static bool pairs_enabled() {
+    const char* e = std::getenv("GC_PAIRS");
+    return !(e && std::strcmp(e, "0") == 0);
+}
+
+// CTA of each group whose phase cycles the statistics report: the first,
+// or GC_TIMING_CTA (diagnostics: a pipelined job's CTA 1 is a generator).
+static uint32_t timing_cta() {
+    const char* e = std::getenv("GC_TIMING_CTA");
+    return e ? (uint32_t)std::atoi(e) : 0u;
+}
+
 static bool pipeline_enabled() {
     const char* e = std::getenv("GC_PIPELINE");
     return !(e && std::strcmp(e, "0") == 0);
@@ -1207,12 +1310,10 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         G.store_words = L.g_store_words[g];
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
         G.slice_cnt = ws + L.g_slice[g];
-        G.pflags = L.g_pipe[g] ? reinterpret_cast<unsigned long long*>(ws + L.g_pipe[g]) : nullptr;
-        G.accbuf = L.g_pipe[g]
-                       ? reinterpret_cast<uint32_t*>(
-                             ws + L.g_pipe[g] +
-                             align_up(sizeof(unsigned long long) * (2 * (size_t)L.ncta[g] + 1)))
-                       : nullptr;
+        G.pflags = nullptr;
+        G.accbuf = nullptr;
+        G.pairbuf = nullptr;
+        if (L.g_pipe[g]) set_pipe(G, ws + L.g_pipe[g]);
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
@@ -1269,8 +1370,7 @@ int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stre
             cudaSuccess)
             return cuda_fail("group flags");
         if (L.g_pipe[g] &&
-            (e = cudaMemsetAsync(ws + L.g_pipe[g], 0xff,
-                                 sizeof(unsigned long long) * (2 * (size_t)L.ncta[g] + 1),
+            (e = cudaMemsetAsync(ws + L.g_pipe[g], 0xff, pipe_flag_bytes(L.ncta[g] + 1),
                                  stream)) != cudaSuccess)
             return cuda_fail("pipeline flags");
     }
@@ -1285,6 +1385,8 @@ int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stre
     a.cache_words = L.cache_words;
     a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
     a.resolve_block = resolve_block_size();
+    a.pairs = pairs_enabled() ? 1u : 0u;
+    a.timing_cta = timing_cta();
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel(kernel, dim3(L.grid), dim3(kBlock), args, L.smem_bytes,
                                     stream);
@@ -1343,8 +1445,7 @@ bool serve_layout(const gc_server_config& cfg, ServeLayout* L, std::string* why)
         L->g_bitmap[g] = off; off += align_up((L->bitmap_bits + 31) / 32 * 4);
         L->g_slice[g] = off;  off += align_up((size_t)2 * G * kMaxSlices);
         L->g_pipe[g] = off;
-        off += align_up(sizeof(unsigned long long) * (2 * (size_t)G + 1));
-        off += align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap);
+        off += pipe_bytes(G);
     }
     L->off_hball = off;
     L->hball_bytes = 64ull << 20;
@@ -1452,9 +1553,7 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
         G.store_words = L.store_words;
         G.bitmap = reinterpret_cast<uint32_t*>(ws + L.g_bitmap[g]);
         G.slice_cnt = ws + L.g_slice[g];
-        G.pflags = reinterpret_cast<unsigned long long*>(ws + L.g_pipe[g]);
-        G.accbuf = reinterpret_cast<uint32_t*>(
-            ws + L.g_pipe[g] + align_up(sizeof(unsigned long long) * (2 * (size_t)G.ncta + 1)));
+        set_pipe(G, ws + L.g_pipe[g]);
     }
     cudaError_t e;
     auto cuda_fail = [&](const char* what) {
@@ -1471,8 +1570,7 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
                                  sizeof(unsigned long long) * 2 * (L.group_ctas + 1), stream)) !=
             cudaSuccess)
             return cuda_fail("group flags");
-        if ((e = cudaMemsetAsync(ws + L.g_pipe[g], 0xff,
-                                 sizeof(unsigned long long) * (2 * (size_t)L.group_ctas + 1),
+        if ((e = cudaMemsetAsync(ws + L.g_pipe[g], 0xff, pipe_flag_bytes(L.group_ctas),
                                  stream)) != cudaSuccess)
             return cuda_fail("pipeline flags");
     }
@@ -1493,6 +1591,8 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
     a.cache_words = L.cache_words;
     a.timeout_cycles = 20000000000ll;
     a.resolve_block = resolve_block_size();
+    a.pairs = pairs_enabled() ? 1u : 0u;
+    a.timing_cta = timing_cta();
     int dev = 0, clk_khz = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);

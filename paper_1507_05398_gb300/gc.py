@@ -78,7 +78,8 @@ class Stats(ctypes.Structure):
                 ("dense_tests", ctypes.c_uint64), ("executed_tests", ctypes.c_uint64),
                 ("marks", ctypes.c_uint64), ("windows", ctypes.c_uint64),
                 ("survivors", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("strategy", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 12)]
+                ("strategy", ctypes.c_int32), ("phase_cycles", ctypes.c_uint64 * 12),
+                ("pair_windows", ctypes.c_uint64), ("pair_fallbacks", ctypes.c_uint64)]
 
     PHASES = ("mark", "generate", "test_new", "test_old", "wait", "gather", "resolve", "commit",
               "res_matrix", "res_rounds", "res_append_kill", "rounds")

@@ -98,3 +98,41 @@ def test_bitmap_scan(ordname):
             got, found = g.bitmap_scan(n, ordname, w, dev(bm), r0, cnt)
             assert found == len(want)
             assert host(got).tolist() == want.tolist()
+
+
+def _few_conflict_lists():
+    """Lists for the bucketed resolver: runs of a code with stray vectors
+    dropped in (the shape of a late window of a large sweep), random wide
+    vectors with near copies, ragged sizes; then the shapes where it gives up
+    (too many conflicts, too few varying bits, too many bucket pairs)."""
+    out = []
+    rng = np.random.default_rng(7)
+    ham = oracle.greedy_ball(20, 3, "lex").astype(np.uint32)
+    for size, stray, d in [(1000, 30, 3), (4096 - 64, 64, 3), (33, 2, 3), (31, 0, 2)]:
+        run = ham[5000:5000 + size]
+        extra = rng.integers(int(run[0]), int(run[-1]) + 1, stray, dtype=np.uint64)
+        extra = np.setdiff1d(extra.astype(np.uint32), run)
+        keys = np.concatenate([np.arange(len(run), dtype=float),
+                               rng.uniform(0, len(run), len(extra))])
+        lst = np.concatenate([run, extra])[np.argsort(keys, kind="stable")]
+        out.append((f"hamming-run{size}+{len(extra)}", d, lst))
+    for n_items, d in [(1, 4), (2, 8), (1000, 8), (4096, 8), (777, 6), (1500, 4)]:
+        base = rng.integers(0, 1 << 32, n_items, dtype=np.uint64).astype(np.uint32)
+        for i in rng.choice(n_items, n_items // 20, replace=False):
+            flips = rng.choice(32, int(rng.integers(1, d + 1)), replace=False)
+            base[i] = base[rng.integers(0, n_items)] ^ np.uint32(sum(1 << int(f) for f in flips))
+        out.append((f"random32-{n_items}-d{d}", d, np.unique(base)[rng.permutation(len(np.unique(base)))]))
+    out.append(("all12-d3", 3, rng.permutation(4096).astype(np.uint32)))
+    out.append(("few-bits-d5", 5, (np.arange(8, dtype=np.uint32) * 3) | np.uint32(0xABC00000)))
+    out.append(("8bits-d8", 8, rng.permutation(256).astype(np.uint32)))
+    return out
+
+
+@pytest.mark.parametrize("sparse", ["1", "0"])
+@pytest.mark.parametrize("case", _few_conflict_lists(), ids=lambda c: c[0])
+def test_resolve_few_conflicts(case, sparse, monkeypatch):
+    _, d, lst = case
+    monkeypatch.setenv("GC_SPARSE", sparse)
+    want = oracle.resolve(d, lst)
+    got = G().resolve(d, dev(lst)).cpu().numpy()
+    assert got.tolist() == want.tolist()

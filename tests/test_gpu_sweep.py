@@ -133,3 +133,34 @@ def test_large_configs_against_stored_oracle(row):
         assert hashlib.sha256(got.astype("<u4").tobytes()).hexdigest() == row["sha256"]
     if (n, d, o) == (31, 3, "lex"):
         assert len(got) == 2 ** 26 and np.all(np.diff(got.astype(np.int64)) > 0)
+
+
+# (n, d, order, strategy, survivor target, whether pair lists must decide
+# some window of a whole-GPU launch)
+PAIR_CASES = [
+    (20, 3, "lex", "bitmap", 2048, True),
+    (22, 3, "grlex", "bitmap", 1024, True),
+    (23, 7, "lex", "bitmap", 1024, True),
+    (19, 4, "grlex", "bitmap", 1024, False),
+    (16, 2, "gray", "bitmap", 1024, False),
+    (20, 3, "gray", "distance", 2048, False),
+]
+
+
+@pytest.mark.parametrize("case", PAIR_CASES, ids=lambda c: f"n{c[0]}d{c[1]}{c[2]}-{c[3]}")
+def test_generator_pair_lists(case, monkeypatch):
+    """Pipelined bitmap jobs in a large group decide a window from the list
+    of its conflicting pairs that the generator CTAs found, after a window
+    that accepted at least 7/8 of its survivors (GC_PAIRS=0 turns it off).
+    The code is the oracle's either way, and on the codes with such windows
+    the pair lists decide some of them."""
+    n, d, o, strategy, target, expect = case
+    want = oracle.greedy_ball(n, d, o)
+    for pairs in ("1", "0"):
+        monkeypatch.setenv("GC_PAIRS", pairs)
+        got, st = gpu_code(n, d, o, -1, strategy, survivor_target=target)
+        assert got.tolist() == want.tolist(), pairs
+        if pairs == "0" or strategy == "distance":
+            assert st.pair_windows == 0 and st.pair_fallbacks == 0
+        elif expect:
+            assert st.pair_windows > 0
