@@ -390,9 +390,10 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
 // ------------------------------------------------------------ pair resolver
 // CTA-wide, narrow words.  Decides the list x[0..n) (n <= 4096) in order,
 // as the serial greedy would (Section 4), from the list of its conflicting
-// pairs: pairs[e] = (k << 16) | i for entries k < i within distance d-1 (or
-// otherwise in conflict); every conflicting pair must be listed, duplicates
-// are harmless.  Rounds: an undecided entry with an accepted earlier
+// pairs (k, i), k < i, entries within distance d-1 (or otherwise in
+// conflict); every conflicting pair must be listed, duplicates are
+// harmless.  for_pairs(f) calls f(k, i) for this thread's share of the
+// pairs (every pair in exactly one thread).  Rounds: an undecided entry with an accepted earlier
 // neighbour is rejected, one whose earlier neighbours are all rejected is
 // accepted; the first undecided entry always decides, so the rounds end, and
 // every decision rests on final ones.  Accepted entries are appended in
@@ -400,10 +401,11 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
 //   state  n bytes, flags 2 * 4096 bytes of scratch
 // tim (optional, thread 0): cycles to tim[1] rounds and tim[2] append,
 // tim[3] counts rounds.
+template <typename ForPairs>
 __device__ __forceinline__ uint32_t pair_resolve(BlockScratch& bs, const uint32_t* x,
                                                  const uint32_t* off, uint8_t* state, uint32_t n,
-                                                 const uint32_t* pairs, uint32_t np,
-                                                 uint8_t* flags, uint32_t* acc, uint32_t* acc_off,
+                                                 ForPairs for_pairs, uint8_t* flags,
+                                                 uint32_t* acc, uint32_t* acc_off,
                                                  unsigned long long* tim = nullptr) {
     const int lane = lane_id();
     const bool timing = tim && threadIdx.x == 0;
@@ -422,14 +424,13 @@ __device__ __forceinline__ uint32_t pair_resolve(BlockScratch& bs, const uint32_
         // this round's flag slot; the next one was last read two rounds ago
         const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
         if (threadIdx.x == 0) bs.left[next] = 0u;
-        for (uint32_t e = threadIdx.x; e < np; e += kBlock) {
-            const uint32_t k = pairs[e] >> 16, i = pairs[e] & 0xffffu;
+        for_pairs([&](uint32_t k, uint32_t i) {
             if (state[i] == 0) {
                 const uint8_t sk = state[k];
                 if (sk == 1) killed[i] = 1;
                 else if (sk == 0) blocked[i] = 1;
             }
-        }
+        });
         __syncthreads();
         // decide, and clear the marks for the next round (the thread that
         // reads an entry's marks is the one that clears them)
@@ -594,7 +595,12 @@ __device__ __forceinline__ bool sparse_resolve(BlockScratch& bs, const uint32_t*
     if (ne > kSpEdges) return false;
     uint8_t* killed = reinterpret_cast<uint8_t*>(scratch + 2 * kSpBuckets);  // [n]
     tick(0);
-    *nacc_out = pair_resolve(bs, x, off, state, n, edges, ne, killed, acc, acc_off, tim);
+    *nacc_out = pair_resolve(
+        bs, x, off, state, n,
+        [&](auto&& f) {
+            for (uint32_t e = threadIdx.x; e < ne; e += kBlock) f(edges[e] >> 16, edges[e] & 0xffffu);
+        },
+        killed, acc, acc_off, tim);
     return true;
 }
 

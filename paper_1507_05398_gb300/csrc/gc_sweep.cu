@@ -60,6 +60,8 @@ constexpr int kSurvCap = 4096;     // survivors resolved per window
 // Pipelined windows: conflicting pairs one generator may publish, and pairs
 // the resolver takes into shared memory (behind 8 KiB of round flags in the
 // resolver matrix); more and the window goes to the conflict matrices.
+// (Rounds that read longer lists from the generators' buffers in L2 were
+// latency-bound: ~160 us per window against ~34 us for the matrices.)
 constexpr uint32_t kPairCap = 2048;
 constexpr uint32_t kPairShared = 6144;
 // Generators list the conflicts only in groups with at least this many of
@@ -114,7 +116,8 @@ struct BatchArgs {
     uint32_t cache_words;
     long long timeout_cycles;
     uint32_t resolve_block;       // entries per conflict matrix (<= kResolveBlock)
-    uint32_t pairs;               // 1: pipelined generators list each window's conflicts
+    uint32_t pairs;               // pipelined generators list each window's conflicts:
+                                  // 0 never, 1 when it pays, 2 always
     uint32_t timing_cta;          // CTA of each group whose phases are timed
     ServeQueue queue;             // used when queue.descs != nullptr
 };
@@ -602,7 +605,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                         const uint32_t np = s.bs.sp_edges;
                         st_release_u64(eflag + (size_t)par * G + gi,
                                        ((unsigned long long)wseq << 32) |
-                                           (np > kPairCap ? kPairShared + 1u : np));
+                                           (np > kPairCap ? kPairCap + 1u : np));
                     }
                     mark_phase(6);
                 }
@@ -629,19 +632,30 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                                                          a.err, a.timeout_cycles, &ok);
                         if (!ok) break;
                         mark_phase(4);
-                        if (np <= kPairShared) {
+                        // a generator whose pairs overflowed its buffer, or more
+                        // pairs than shared memory takes: conflict matrices
+                        bool over = false;
+                        for (int g = tid; g < nG; g += kBlock)
+                            over |= s.pref[g + 1] - s.pref[g] > kPairCap;
+                        over = __syncthreads_or(over) || np > kPairShared;
+                        if (!over) {
                             uint32_t* pr = &s.M[0][0] + 2048;  // after 8 KiB of round flags
+                            const uint32_t* pbuf = grp.pairbuf + (size_t)par * G * kPairCap;
                             for (int g = warp; g < nG; g += kWarps) {
                                 const uint32_t p0 = s.pref[g], c = s.pref[g + 1] - p0;
-                                const uint32_t* src = grp.pairbuf + ((size_t)par * G + g) * kPairCap;
+                                const uint32_t* src = pbuf + (size_t)g * kPairCap;
                                 for (uint32_t i = lane; i < c; i += 32) pr[p0 + i] = ld_cg(src + i);
                             }
                             __syncthreads();
                             if constexpr (!kWide)  // pipelining is for narrow words
-                                nacc = pair_resolve(s.bs, s.list_x, s.list_off, s.dead, Suse, pr,
-                                                    np, reinterpret_cast<uint8_t*>(&s.M[0][0]),
-                                                    cur, s.acc_off,
-                                                    timing ? s.phase + 8 : nullptr);
+                                nacc = pair_resolve(
+                                    s.bs, s.list_x, s.list_off, s.dead, Suse,
+                                    [&](auto&& f) {
+                                        for (uint32_t e = tid; e < np; e += kBlock)
+                                            f(pr[e] >> 16, pr[e] & 0xffffu);
+                                    },
+                                    reinterpret_cast<uint8_t*>(&s.M[0][0]), cur, s.acc_off,
+                                    timing ? s.phase + 8 : nullptr);
                             decided = true;
                             ++pair_done;
                         } else {
@@ -659,8 +673,9 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     }
                     __threadfence();
                     __syncthreads();
-                    pairs_on = a.pairs != 0u && nG >= kPairMinGenerators &&
-                               8u * (Suse - nacc) <= Suse;
+                    pairs_on = a.pairs == 2u ||
+                               (a.pairs == 1u && nG >= kPairMinGenerators &&
+                                8u * (Suse - nacc) <= Suse);
                     if (tid == 0)
                         st_release_u64(rflag, ((unsigned long long)wseq << 32) |
                                                   (pairs_on ? 0x80000000ull : 0ull) | nacc);
@@ -1242,10 +1257,12 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
 // GC_PIPELINE=0 runs bitmap jobs with the sequential window loop (for
 // measurements); pipelining is on by default.
 // Pipelined windows: the generators list the window's conflicting pairs for
-// the resolver; GC_PAIRS=0 turns it off (measurements).
-static bool pairs_enabled() {
+// the resolver when that pays; GC_PAIRS=0 turns it off, GC_PAIRS=2 makes it
+// unconditional (measurements, tests).
+static uint32_t pairs_mode() {
     const char* e = std::getenv("GC_PAIRS");
-    return !(e && std::strcmp(e, "0") == 0);
+    if (!e) return 1u;
+    return std::strcmp(e, "0") == 0 ? 0u : std::strcmp(e, "2") == 0 ? 2u : 1u;
 }
 
 // CTA of each group whose phase cycles the statistics report: the first,
@@ -1385,7 +1402,7 @@ int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stre
     a.cache_words = L.cache_words;
     a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
     a.resolve_block = resolve_block_size();
-    a.pairs = pairs_enabled() ? 1u : 0u;
+    a.pairs = pairs_mode();
     a.timing_cta = timing_cta();
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel(kernel, dim3(L.grid), dim3(kBlock), args, L.smem_bytes,
@@ -1591,7 +1608,7 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
     a.cache_words = L.cache_words;
     a.timeout_cycles = 20000000000ll;
     a.resolve_block = resolve_block_size();
-    a.pairs = pairs_enabled() ? 1u : 0u;
+    a.pairs = pairs_mode();
     a.timing_cta = timing_cta();
     int dev = 0, clk_khz = 0;
     cudaGetDevice(&dev);

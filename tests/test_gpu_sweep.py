@@ -151,16 +151,18 @@ PAIR_CASES = [
 def test_generator_pair_lists(case, monkeypatch):
     """Pipelined bitmap jobs in a large group decide a window from the list
     of its conflicting pairs that the generator CTAs found, after a window
-    that accepted at least 7/8 of its survivors (GC_PAIRS=0 turns it off).
+    that accepted at least 7/8 of its survivors (GC_PAIRS=0 turns it off,
+    GC_PAIRS=2 lists every window's pairs).
     The code is the oracle's either way, and on the codes with such windows
     the pair lists decide some of them."""
     n, d, o, strategy, target, expect = case
     want = oracle.greedy_ball(n, d, o)
-    for pairs in ("1", "0"):
+    for pairs in ("1", "0", "2"):
         monkeypatch.setenv("GC_PAIRS", pairs)
         got, st = gpu_code(n, d, o, -1, strategy, survivor_target=target)
         assert got.tolist() == want.tolist(), pairs
         if pairs == "0" or strategy == "distance":
             assert st.pair_windows == 0 and st.pair_fallbacks == 0
-        elif expect:
+        elif pairs == "2" or expect:
+            # GC_PAIRS=2: every window after the first goes through the lists
             assert st.pair_windows > 0
