@@ -26,6 +26,7 @@ __all__ = [
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
     "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
     "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
+    "batch_result_bytes", "clear_batch_cache",
     "ServerConfig", "Server", "autotune", "set_tune_cache",
 ]
 
@@ -290,13 +291,32 @@ def noalloc_scratch_bytes() -> int:
 _STRAT = {None: 0, "auto": 0, "distance": 1, "bitmap": 2}
 
 
+def _flat_layout(njobs, caps):
+    """Byte offsets of each output in a batch's flat buffer (statistics
+    first, 256-byte aligned pieces) and the buffer's size."""
+    al = lambda v: (v + 255) & ~255  # noqa: E731
+    offs, off = [], al(njobs * ctypes.sizeof(Stats))
+    for c in caps:
+        offs.append(off)
+        off += al(4 * max(c, 1))
+    return offs, off
+
+
+def batch_result_bytes(problems) -> int:
+    """Bytes one results() call copies back for this batch."""
+    ps = [tuple(p) + (None,) * (6 - len(p)) for p in problems]
+    return _flat_layout(len(ps), [_bound(n, d, w, c) for n, d, o, w, _, c in ps])[1]
+
+
 class BatchBuffers:
     """Device buffers (outputs, stats, workspace) for a batch of problems,
     prepared once (gc_batch_create) and launched any number of times
     (gc_batch_launch), directly or as a captured CUDA graph.
 
     problems: list of (n, d, ordering, weight[, strategy[, constraint]]).
-    Allocated once through torch's caching allocator."""
+    The statistics and every output live in one device buffer (so results()
+    is one copy back, into a pinned host buffer); allocated once through
+    torch's caching allocator."""
 
     def __init__(self, problems, ngroups=0, device=None):
         import torch
@@ -304,9 +324,13 @@ class BatchBuffers:
         self.problems = [tuple(p) + (None,) * (6 - len(p)) for p in problems]
         self.ngroups = ngroups
         self.caps = [_bound(n, d, w, c) for n, d, o, w, _, c in self.problems]
-        self.outs = [torch.empty(max(c, 1), dtype=torch.int32, device=dev) for c in self.caps]
-        self.stats = torch.zeros((len(self.problems), ctypes.sizeof(Stats)), dtype=torch.uint8,
-                                 device=dev)
+        nj, sbytes = len(self.problems), ctypes.sizeof(Stats)
+        self._offs, off = _flat_layout(nj, self.caps)
+        self._flat = torch.zeros(off, dtype=torch.uint8, device=dev)
+        self._host = torch.empty(off, dtype=torch.uint8, pin_memory=True)
+        self.stats = self._flat[:nj * sbytes].view(nj, sbytes)
+        self.outs = [self._flat[o:o + 4 * max(c, 1)].view(torch.int32)
+                     for o, c in zip(self._offs, self.caps)]
         self.jobs = (Job * len(self.problems))()
         for k, (n, d, o, w, st, c) in enumerate(self.problems):
             j = self.jobs[k]
@@ -348,13 +372,22 @@ class BatchBuffers:
             _lib.gc_batch_destroy(h)
             self._handle = None
 
-    def results(self):
-        """[(code uint32 numpy array, Stats)] after the stream has finished."""
-        host_stats = self.stats.cpu().numpy()
+    def results(self, stream=None):
+        """[(code uint32 numpy array, Stats)]: one copy of the statistics and
+        the outputs back to the host, ordered after the work on `stream`
+        (default: the current stream), which it then waits for."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            self._host.copy_(self._flat, non_blocking=True)
+        st.synchronize()
+        h = self._host.numpy()
+        sbytes = ctypes.sizeof(Stats)
         out = []
         for k in range(len(self.problems)):
-            s = Stats.from_buffer_copy(host_stats[k].tobytes())
-            code = self.outs[k][:min(s.codewords, self.caps[k])].cpu().numpy().view(np.uint32)
+            s = Stats.from_buffer_copy(h[k * sbytes:(k + 1) * sbytes].tobytes())
+            m = min(s.codewords, self.caps[k])
+            code = h[self._offs[k]:self._offs[k] + 4 * m].view(np.uint32).copy()
             out.append((code, s))
         return out
 
@@ -369,13 +402,35 @@ def batch_generate_async(jobs, ngroups, workspace, stream=None):
            "gc_batch_generate_async")
 
 
+_batch_cache: dict = {}
+_batch_lock = threading.Lock()
+_BATCH_CACHE_SIZE = 4
+
+
+def clear_batch_cache():
+    """Drops the prepared batches generate_batch keeps (and their memory)."""
+    with _batch_lock:
+        _batch_cache.clear()
+
+
 def generate_batch(problems, ngroups=0, stream=None):
-    """Generate many codes in one launch; returns [(code, Stats)]."""
+    """Generate many codes in one launch; returns [(code, Stats)] with the
+    codes as host arrays.  The prepared batch (plan, workspace, ball tables,
+    buffers) is kept for the next call with the same problems, grouping,
+    device and GC_* environment (the last few such sets; clear_batch_cache()
+    drops them), so a repeated call is one launch and one copy back."""
     import torch
-    buf = BatchBuffers(problems, ngroups)
-    buf.launch(stream)
-    torch.cuda.synchronize()
-    return buf.results()
+    key = (tuple(tuple(p) for p in problems), ngroups, torch.cuda.current_device(),
+           tuple(sorted((k, v) for k, v in os.environ.items() if k.startswith("GC_"))))
+    with _batch_lock:
+        buf = _batch_cache.pop(key, None)
+        if buf is None:
+            buf = BatchBuffers(problems, ngroups)
+        _batch_cache[key] = buf  # most recent last
+        while len(_batch_cache) > _BATCH_CACHE_SIZE:
+            _batch_cache.pop(next(iter(_batch_cache)))
+        buf.launch(stream)
+        return buf.results(stream)
 
 
 def stats_from(t) -> Stats:

@@ -32,6 +32,26 @@ def test_bench_workload_as_one_batch(ngroups):
         assert st.dense_tests == oracle.dense_tests(pos, 1 << n)
 
 
+def test_generate_batch_keeps_the_prepared_batch(monkeypatch):
+    """A repeated generate_batch call reuses the prepared batch (one launch
+    and one copy back) and returns the oracle's codes every time; another
+    GC_* environment prepares its own."""
+    g = G()
+    g.clear_batch_cache()
+    probs = [(16, 3, "lex", -1), (14, 4, "grevlex", -1), (13, 3, "gray", 5)]
+    want = [oracle.greedy_ball(n, d, o, w).tolist() for n, d, o, w in probs]
+    for _ in range(3):
+        res = g.generate_batch(probs, ngroups=2)
+        assert [c.tolist() for c, _ in res] == want
+        assert all(st.status == 0 and st.codewords == len(c) for c, st in res)
+    assert len(g.gc._batch_cache) == 1
+    monkeypatch.setenv("GC_PAIRS", "2")
+    assert [c.tolist() for c, _ in g.generate_batch(probs, ngroups=2)] == want
+    assert len(g.gc._batch_cache) == 2
+    g.clear_batch_cache()
+    assert len(g.gc._batch_cache) == 0
+
+
 def test_batch_handle_relaunch_and_cuda_graph():
     """gc_batch_create once, then gc_batch_launch several times, then the
     launch captured into a CUDA graph and replayed: every run rewrites the
