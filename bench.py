@@ -52,7 +52,10 @@ def cpu_model() -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms.  Entering
+    waits for the first sample (so sampling is running when the timed region
+    starts); leaving waits for one sample after the region ends.  summary()
+    covers the samples from the region's start to that one."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -62,26 +65,48 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
 
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self._got.append((time.monotonic(), line))
+
+    def _wait_for(self, pred, timeout):
+        end = time.monotonic() + timeout
+        while time.monotonic() < end and not pred():
+            time.sleep(0.005)
+
     def __enter__(self):
+        import threading
+        self._got, self.lines = [], []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._reader = threading.Thread(target=self._read, daemon=True)
+            self._reader.start()
+            self._wait_for(lambda: self._got, 5.0)
         except Exception:
             self.proc = None
+        self.t0 = time.monotonic()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        t1 = time.monotonic()
         if self.proc is not None:
+            self._wait_for(lambda: self._got and self._got[-1][0] > t1, 1.0)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self._reader.join(timeout=2)
+            after = [ts for ts, _ in self._got if ts > t1]
+            t_end = after[0] if after else t1
+            # the last sample before the region, those inside it, the first after
+            before = [ts for ts, _ in self._got if ts <= self.t0]
+            t_beg = before[-1] if before else self.t0
+            self.lines = [l for ts, l in self._got if t_beg <= ts <= t_end]
 
     def summary(self):
         sm, mx, reasons = [], None, set()
@@ -347,8 +372,10 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 300, about 1 s; 5 for --impl reference)")
+    ap.add_argument("--warmup", type=int, default=None,
+                    help="untimed warm-up steps (default: 10; 3 for --impl reference)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API leg")
@@ -357,6 +384,11 @@ def main():
     ap.add_argument("--only", default=None,
                     help="run one code instead of the workload, e.g. '24,8,lex' (profiling)")
     args = ap.parse_args()
+    ref = args.impl == "reference"
+    if args.steps is None:
+        args.steps = 5 if ref else 300
+    if args.warmup is None:
+        args.warmup = 3 if ref else 10
     if args.impl == "reference":
         run_reference(args)
     else:
