@@ -343,6 +343,11 @@ def run_ours(args):
         "batched_speedup_vs_one_launch_per_code": single_ms / mean_step_ms,
         "dense_tests_per_step": dense, "executed_tests_per_step": executed,
         "windows_per_step": sum(st.windows for st in stats_now),
+        # the bitmap path's own measure: ball-mark word ORs (L2 atomics) per
+        # step and per second of the step; the n = 20 bitmaps are 128 KiB and
+        # stay in L2, so no HBM figure applies to them
+        "bitmap_marks_per_step": sum(st.marks for st in stats_now),
+        "bitmap_marks_per_s": sum(st.marks for st in stats_now) / (mean_step_ms * 1e-3),
         "survivors_per_step": sum(st.survivors for st in stats_now),
         "phase_ms_cta0": {f"n={n} d={d} {o}": dict(
             {ph: (c if ph in ("rounds", "blocks") else round(1e3 * c / clock_hz, 4))

@@ -38,6 +38,7 @@ def test_generate_batch_keeps_the_prepared_batch(monkeypatch):
     GC_* environment prepares its own."""
     g = G()
     g.clear_batch_cache()
+    monkeypatch.delenv("GC_PAIRS", raising=False)
     probs = [(16, 3, "lex", -1), (14, 4, "grevlex", -1), (13, 3, "gray", 5)]
     want = [oracle.greedy_ball(n, d, o, w).tolist() for n, d, o, w in probs]
     for _ in range(3):
