@@ -111,7 +111,10 @@ typedef struct {
     int block;             /* threads per CTA (multiple of 32, <= 1024) */
     uint32_t window_min;   /* smallest window of ranks tested per step */
     uint32_t window_max;   /* largest window */
-    uint32_t survivor_target; /* window sizing aims at this many survivors */
+    uint32_t survivor_target; /* window sizing aims at this many survivors
+                                 (gc_plan: 512 distance, 1024 bitmap; 4096
+                                 lex/Gray and 2048 graded for bitmap sweeps
+                                 of >= 2^28 candidates) */
 } gc_plan_t;
 
 /* Counters filled by the sweep (device-side writes, read after sync). */

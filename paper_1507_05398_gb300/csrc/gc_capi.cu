@@ -175,11 +175,11 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
         pl->strategy = GC_STRATEGY_BITMAP;
     else
         pl->strategy = GC_STRATEGY_DISTANCE;
-    pl->survivor_target = default_target(pl->strategy);
+    pl->survivor_target = default_target(pl->strategy, p);
     if (const char* e = std::getenv("GC_STRATEGY")) {
         if (!std::strcmp(e, "distance")) pl->strategy = GC_STRATEGY_DISTANCE;
         if (!std::strcmp(e, "bitmap")) pl->strategy = GC_STRATEGY_BITMAP;
-        pl->survivor_target = default_target(pl->strategy);
+        pl->survivor_target = default_target(pl->strategy, p);
     }
 }
 
@@ -188,7 +188,7 @@ static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* o
     if (in) {
         if (in->strategy != GC_STRATEGY_AUTO && !p.orth) {
             out->strategy = in->strategy;
-            out->survivor_target = default_target(in->strategy);
+            out->survivor_target = default_target(in->strategy, p);
         }
         if (in->grid > 0) out->grid = in->grid;
         if (in->window_min) out->window_min = in->window_min;

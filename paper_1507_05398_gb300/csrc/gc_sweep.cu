@@ -1302,7 +1302,7 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
                                              : nullptr;
         D.hball_len = D.strategy == kStratBitmap ? (uint32_t)high_ball_len(J.p.n, J.p.d) : 0u;
         D.target = J.plan.survivor_target ? J.plan.survivor_target
-                                          : default_target(J.plan.strategy);
+                                          : default_target(J.plan.strategy, J.p);
         // a window never holds more candidates than the group's chunks
         int g = 0;
         for (int q = 0; q < L.ngroups; ++q)
@@ -1519,7 +1519,7 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
     D->out = d_out;
     D->cap = cap;
     D->stats = d_stats;
-    D->target = default_target(pl.strategy);
+    D->target = default_target(pl.strategy, p);
     D->wmax = (uint32_t)((uint64_t)L.group_ctas * kChunk);
     D->wmin = std::min<uint32_t>(256, D->wmax);
     if (D->strategy == kStratBitmap && p.d >= 1) {
