@@ -180,7 +180,34 @@ def cpu_baseline_sample():
                       f"{secs:.1f} s)", "cpu": cpu_model()}
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source with comments removed and whitespace runs collapsed
+    (string and character literals kept as written)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the CUDA/C++ sources' code (comments and layout ignored): the
+    recorded DRAM traffic stays valid across comment-only edits."""
     import glob
     import hashlib
     csrc = os.path.join(ROOT, "paper_1507_05398_gb300", "csrc")
@@ -189,7 +216,7 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+        h.update(_code_only(open(f, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

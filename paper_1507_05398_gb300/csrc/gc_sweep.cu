@@ -32,7 +32,11 @@
 //    slices round-robin instead of one chunk per CTA, because the test cost
 //    per candidate is very uneven along the order;
 //  - bitmap jobs on three or more CTAs run pipelined: the group's first CTA
-//    resolves window t while the others generate and filter window t+1.
+//    resolves window t while the others generate and filter window t+1;
+//  - in pipelined groups of 64 or more generators, after a window that
+//    accepted at least 7/8 of its survivors, the generators also list the
+//    next window's conflicting pairs between them, and the resolver decides
+//    it in rounds over that list (pair_resolve) instead of conflict matrices.
 // The kernel is instantiated for narrow vectors (uint32 words, n <= 32, both
 // strategies) and wide ones (uint64 words, n <= 64, distance strategy only).
 #include <algorithm>
