@@ -166,3 +166,13 @@ def test_generator_pair_lists(case, monkeypatch):
         elif pairs == "2" or expect:
             # GC_PAIRS=2: every window after the first goes through the lists
             assert st.pair_windows > 0
+
+
+def test_pair_list_overflow_falls_back_to_matrices(monkeypatch):
+    """GC_PAIRS=2 on n = 20, d = 4 grevlex (windows with thousands of
+    conflicting pairs): some windows are decided from the lists, the rest
+    overflow them and go to the conflict matrices; the code is the oracle's."""
+    monkeypatch.setenv("GC_PAIRS", "2")
+    got, st = gpu_code(20, 4, "grevlex", -1, "bitmap")
+    assert got.tolist() == oracle.greedy_ball(20, 4, "grevlex").tolist()
+    assert st.pair_windows > 0 and st.pair_fallbacks > 0
