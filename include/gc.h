@@ -256,10 +256,13 @@ typedef struct {
 size_t gc_batch_workspace_size(const gc_job *jobs, int njobs, int ngroups);
 
 /* Generates every job's code (Section 4) in ONE persistent cooperative
- * launch.  The SMs are split into ngroups groups of equal size (ngroups <= 0:
- * one group per job, at most one per SM); jobs are assigned to groups longest
- * first (by an estimate of their work) and each group sweeps its jobs one
- * after the other, so independent codes run concurrently on disjoint SMs.
+ * launch.  The SMs are split into ngroups groups (ngroups <= 0: one group per
+ * job, sized by an estimate of its work, for batches of up to a quarter as
+ * many jobs as SMs; groups of four SMs otherwise).  With one job per group
+ * every job runs at once on its own SMs; with more jobs than groups the
+ * groups are of equal size and each claims the next job, longest first, as
+ * it becomes free (GC_BATCH_DYNAMIC=0: a fixed longest-first assignment), so
+ * independent codes run concurrently on disjoint SMs.
  * Each job's result equals what gc_generate_async gives for it alone.
  * workspace: device, >= gc_batch_workspace_size() bytes, 256-byte aligned,
  * owned by the caller.  Per-job status is in its gc_stats. */

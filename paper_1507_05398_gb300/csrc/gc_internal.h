@@ -118,6 +118,7 @@ struct BatchJob {
 struct BatchLayout {
     int grid = 0, ngroups = 0;
     bool wide = false;          // the uint64-word kernel
+    bool dynamic = false;       // groups claim jobs (longest first) as they free up
     uint32_t cache_words = 0;   // shared-memory code cache (distance jobs)
     size_t smem_bytes = 0;
     std::vector<int> first_cta, ncta, job_begin, job_end, job_order;
