@@ -15,6 +15,19 @@ constexpr int kBlock = 1024;           // threads per CTA
 constexpr int kWarps = kBlock / 32;
 constexpr int kResolveBlock = 512;     // candidates per conflict matrix
 constexpr int kResolveWords = kResolveBlock / 32;
+// Whole-window conflict matrices (dense_build / dense_resolve): at most
+// kDenseMaxRows entries, kDenseWords 32-bit words per row.
+constexpr int kDenseMaxRows = 1536;
+constexpr int kDenseWords = kDenseMaxRows / 32;
+
+// Words of the strict lower triangle of the conflict matrix of P entries in
+// the column-word layout of dense_build: column word w (bits for entries
+// 32w..32w+31) is stored for rows 32w..P-1, so it takes P - 32w words.
+__host__ __device__ constexpr uint32_t dense_tri_words(uint32_t P) {
+    return ((P + 31u) / 32u) * P - 16u * ((P + 31u) / 32u) * ((P + 31u) / 32u - 1u);
+}
+constexpr uint32_t kDenseTriMax = dense_tri_words(kDenseMaxRows);
+static_assert(kDenseTriMax % 4 == 0, "matrices are copied in 16-byte pieces");
 
 // Scratch the primitives below need, placed in shared memory by the caller.
 struct BlockScratch {
@@ -232,10 +245,13 @@ __device__ __forceinline__ uint32_t block_filter(BlockScratch& bs, W* x, uint32_
 // decisions of earlier entries, so it is the serial one.  The entries after
 // the block are then tested against the block's accepts and compacted.
 //   x/off[0..n)   candidates in order (modified: compacted)
-//   acc/acc_off   receives accepted vectors/offsets in order (capacity >= n)
+//   acc/acc_off   receives accepted vectors/offsets in order after the
+//                 first acc_start entries, which it leaves as they are
+//                 (capacity >= acc_start + n; acc 16-byte aligned: the kill
+//                 step reads it with 16-byte loads)
 //   Mt            kResolveWords x kResolveBlock words of shared memory
 // block (<= kResolveBlock) sets how many entries one conflict matrix takes.
-// Returns the number accepted.
+// Returns acc_start + the number accepted.
 // tim (optional, thread 0 only): cycles added to tim[0] matrix build,
 // tim[1] rounds, tim[2] append and kill step; tim[3] counts rounds.
 template <bool kOrth = false, typename W>
@@ -244,7 +260,8 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
                                                   W* acc, uint32_t* acc_off,
                                                   uint32_t (*Mt)[kResolveBlock], uint64_t& nt,
                                                   unsigned long long* tim = nullptr,
-                                                  uint32_t block = kResolveBlock) {
+                                                  uint32_t block = kResolveBlock,
+                                                  uint32_t acc_start = 0) {
     constexpr bool orth = kOrth;
     const int lane = lane_id(), warp = warp_id();
     const bool timing = tim && threadIdx.x == 0;
@@ -258,13 +275,13 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
     };
     if (d <= 1 && !orth) {  // nothing conflicts: every candidate is accepted
         for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
-            acc[i] = x[i];
-            if (acc_off) acc_off[i] = off[i];
+            acc[acc_start + i] = x[i];
+            if (acc_off) acc_off[acc_start + i] = off[i];
         }
         __syncthreads();
-        return n;
+        return acc_start + n;
     }
-    uint32_t nacc = 0;
+    uint32_t nacc = acc_start;
     uint32_t start = 0, end = n;
     while (start < end) {
         const uint32_t P = min(block, end - start);
@@ -384,6 +401,147 @@ __device__ __forceinline__ uint32_t block_resolve(BlockScratch& bs, W* x, uint32
         start += P;
         tick(2);
     }
+    return nacc;
+}
+
+// ------------------------------------------------------------ whole-window resolver
+// Word w of row i of a conflict matrix in the column-word layout: with
+// cb(w) = sum over v < w of (P - 32v), minus 32w, it is T[cb(w) + i] for
+// i >= 32w.  cb(0) = 0 and cb(w + 1) = cb(w) + P - 32w - 32.
+
+// No barriers; called by every warp of a CTA.  Builds rows of the strict
+// lower triangle of the conflict matrix of x[0..P) (bit j of row i set iff
+// j < i and the two entries are within distance d-1) into T in the layout
+// above: the row quads q = q0, q0 + qstep, ... (rows 4q..4q+3), a quad per
+// warp, whose four rows share each column load.  A quad never straddles a
+// 32-row word.  Adds the tests to nt.
+__device__ __forceinline__ void dense_build(const uint32_t* x, uint32_t P, int d, uint32_t* T,
+                                            uint32_t q0, uint32_t qstep, uint64_t& nt) {
+    const int lane = lane_id();
+    for (uint32_t q = q0; 4u * q < P; q += qstep) {
+        const uint32_t i0 = 4u * q, nr = min(4u, P - i0);
+        const uint32_t x0 = x[i0];
+        const uint32_t x1 = nr > 1 ? x[i0 + 1] : 0u;
+        const uint32_t x2 = nr > 2 ? x[i0 + 2] : 0u;
+        const uint32_t x3 = nr > 3 ? x[i0 + 3] : 0u;
+        const uint32_t last = i0 >> 5;
+        uint32_t cb = 0;
+        for (uint32_t wd = 0; wd <= last; ++wd) {
+            const uint32_t j = (wd << 5) + lane;
+            const uint32_t c = x[j < P ? j : 0];
+            const unsigned b0 = __ballot_sync(kFull, j < i0 && __popc(x0 ^ c) < d);
+            const unsigned b1 = __ballot_sync(kFull, j < i0 + 1 && __popc(x1 ^ c) < d);
+            const unsigned b2 = __ballot_sync(kFull, j < i0 + 2 && __popc(x2 ^ c) < d);
+            const unsigned b3 = __ballot_sync(kFull, j < i0 + 3 && __popc(x3 ^ c) < d);
+            const unsigned bw = lane == 0 ? b0 : lane == 1 ? b1 : lane == 2 ? b2 : b3;
+            if ((uint32_t)lane < nr) T[cb + i0 + lane] = bw;
+            cb += P - 32u * wd - 32u;
+        }
+        if (lane == 0) nt += 4u * i0 + 6u;
+    }
+}
+
+// CTA-wide, narrow words.  Decides x[0..P) (P <= kDenseMaxRows) in order, as
+// the serial greedy would (Section 4), from the whole strict lower triangle
+// of its conflict matrix T (shared memory, the layout of dense_build).  The
+// rounds are those of block_resolve over one block: an undecided entry with
+// an accepted earlier conflict is rejected, one whose earlier conflicts are
+// all rejected is accepted.  Bits on or above the diagonal are masked, so the
+// first undecided entry always decides and the rounds end whatever T holds.
+// Warp k owns the entries of words k and k + 32.  und/accb: kDenseWords words
+// of shared memory, 16-byte aligned.  Accepted entries are appended in order to acc/acc_off.
+// Returns how many.  tim as for pair_resolve.
+__device__ __forceinline__ uint32_t dense_resolve(BlockScratch& bs, uint32_t* und, uint32_t* accb,
+                                                  const uint32_t* x, const uint32_t* off,
+                                                  uint32_t P, const uint32_t* T, uint32_t* acc,
+                                                  uint32_t* acc_off,
+                                                  unsigned long long* tim = nullptr) {
+    const int lane = lane_id(), warp = warp_id();
+    const bool timing = tim && threadIdx.x == 0;
+    long long t_last = timing ? clock64() : 0;
+    const uint32_t nw = (P + 31u) / 32u;
+    for (uint32_t w = threadIdx.x; w < (uint32_t)kDenseWords; w += kBlock) {
+        const uint32_t wb = w * 32u;
+        und[w] = wb >= P ? 0u : (P - wb >= 32u ? kFull : ((1u << (P - wb)) - 1u));
+        accb[w] = 0u;
+    }
+    if (threadIdx.x < 3) bs.left[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint32_t owners = min(nw, (uint32_t)kWarps);
+    if ((uint32_t)warp < owners) {
+        const unsigned nthreads = owners * 32u;
+        for (uint32_t round = 0;; ++round) {
+            if (timing) tim[3] += 1;
+            // this round's flag slot; the next one was last read two rounds ago
+            const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
+            if (threadIdx.x == 0) bs.left[next] = 0u;
+            unsigned ba[2] = {0u, 0u}, br[2] = {0u, 0u};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t w = (uint32_t)warp + 32u * (uint32_t)k;
+                if (w >= nw) continue;
+                const uint32_t uw = und[w];
+                if (uw == 0u) continue;
+                bool a_now = false, r_now = false;
+                if ((uw >> lane) & 1u) {
+                    const uint32_t i = 32u * w + (uint32_t)lane;
+                    uint32_t kill = 0u, block = 0u, cb = 0u, v = 0u;
+                    // four words at a time: one 16-byte load each of accb, und
+                    for (; v + 4u <= w; v += 4u) {
+                        const uint4 av = *reinterpret_cast<const uint4*>(accb + v);
+                        const uint4 uv = *reinterpret_cast<const uint4*>(und + v);
+                        const uint32_t c1 = cb + P - 32u * v - 32u;
+                        const uint32_t c2 = c1 + P - 32u * v - 64u;
+                        const uint32_t c3 = c2 + P - 32u * v - 96u;
+                        const uint32_t m0 = T[cb + i], m1 = T[c1 + i], m2 = T[c2 + i],
+                                       m3 = T[c3 + i];
+                        kill |= (m0 & av.x) | (m1 & av.y) | (m2 & av.z) | (m3 & av.w);
+                        block |= (m0 & uv.x) | (m1 & uv.y) | (m2 & uv.z) | (m3 & uv.w);
+                        cb = c3 + P - 32u * v - 128u;
+                    }
+                    for (; v < w; ++v) {
+                        const uint32_t m = T[cb + i];
+                        kill |= m & accb[v];
+                        block |= m & und[v];
+                        cb += P - 32u * v - 32u;
+                    }
+                    const uint32_t m = T[cb + i] & ((1u << lane) - 1u);
+                    kill |= m & accb[w];
+                    block |= m & uw;
+                    r_now = kill != 0u;
+                    a_now = !r_now && block == 0u;
+                }
+                ba[k] = __ballot_sync(kFull, a_now);
+                br[k] = __ballot_sync(kFull, r_now);
+            }
+            named_barrier(1, nthreads);
+            if (lane == 0)
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t w = (uint32_t)warp + 32u * (uint32_t)k;
+                    if (w >= nw) continue;
+                    accb[w] |= ba[k];
+                    const uint32_t nu = und[w] & ~(ba[k] | br[k]);
+                    und[w] = nu;
+                    if (nu) bs.left[slot] = 1u;
+                }
+            named_barrier(1, nthreads);
+            if (bs.left[slot] == 0u) break;
+        }
+    }
+    __syncthreads();
+    if (timing) {
+        const long long t = clock64();
+        tim[1] += (unsigned long long)(t - t_last);
+        t_last = t;
+    }
+    uint32_t nacc = 0;
+    for (uint32_t t0 = 0; t0 < P; t0 += kBlock) {
+        const uint32_t i = t0 + threadIdx.x;
+        const bool keep = i < P && ((accb[i >> 5] >> (i & 31u)) & 1u);
+        nacc = block_append(bs, keep, keep ? x[i] : 0u, (keep && acc_off) ? off[i] : 0u, acc,
+                            acc_off, nacc);
+    }
+    if (timing) tim[2] += (unsigned long long)(clock64() - t_last);
     return nacc;
 }
 

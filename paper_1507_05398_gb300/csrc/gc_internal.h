@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdlib>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -35,9 +36,15 @@ struct HostProblem {
 constexpr uint32_t kTargetDistance = 512;
 constexpr uint32_t kTargetBitmap = 1024;
 constexpr uint64_t kLargeSweep = 1ull << 28;
+// GC_TARGET_BITMAP overrides the bitmap target of sweeps below kLargeSweep
+// candidates (measurements).
 inline uint32_t default_target(int strategy, const HostProblem& p) {
     if (strategy != GC_STRATEGY_BITMAP) return kTargetDistance;
-    if (p.valid < kLargeSweep) return kTargetBitmap;
+    if (p.valid < kLargeSweep) {
+        const char* e = std::getenv("GC_TARGET_BITMAP");
+        const int v = e ? std::atoi(e) : 0;
+        return v >= 64 && v <= 4096 ? (uint32_t)v : kTargetBitmap;
+    }
     return (p.ord == GC_ORDER_LEX || p.ord == GC_ORDER_GRAY) ? 4096u : 2048u;
 }
 

@@ -95,6 +95,7 @@ struct GroupDesc {
     unsigned long long* pflags;
     uint32_t* accbuf;
     uint32_t* pairbuf;
+    uint32_t* densebuf;           // pipelined: whole-window conflict matrices [2][kDenseTriMax]
 };
 
 // Serving mode: jobs arrive while the kernel runs.  The host writes a job
@@ -122,6 +123,9 @@ struct BatchArgs {
     uint32_t resolve_block;       // entries per conflict matrix (<= kResolveBlock)
     uint32_t pairs;               // pipelined generators list each window's conflicts:
                                   // 0 never, 1 when it pays, 2 always
+    uint32_t dense_rows;          // pipelined windows: most entries of a whole-window
+                                  // conflict matrix (0: blocked matrices only)
+    uint32_t dense_cut;           // 1: cut such windows at dense_rows survivors
     uint32_t timing_cta;          // CTA of each group whose phases are timed
     unsigned* claim;              // dynamic batches: jobs of job_order handed out so far
     int njobs;                    // dynamic batches: length of job_order
@@ -172,7 +176,6 @@ struct __align__(16) SweepSmem {
     __align__(16) W accA[kSurvCap];
     __align__(16) W accB[kSurvCap];
     __align__(16) uint32_t acc_off[kSurvCap];
-    uint32_t M[kResolveWords][kResolveBlock];
     uint32_t pref[kMaxGroupCtas + 1];
     uint8_t dead[kChunk];
     JobDesc job;
@@ -181,6 +184,11 @@ struct __align__(16) SweepSmem {
     unsigned long long phase[12];  // phase timers (thread 0 of the group's first CTA)
     long long tprev;
     BlockScratch bs;
+    __align__(16) uint32_t dund[kDenseWords];  // whole-window resolver: undecided /
+    __align__(16) uint32_t dacc[kDenseWords];  // accepted bits
+    // Last, so that it runs on into the dynamic code cache: a pipelined
+    // resolver holds a whole-window conflict matrix in M and the cache.
+    __align__(16) uint32_t M[kResolveWords][kResolveBlock];
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
@@ -576,16 +584,26 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                                                 a.timeout_cycles, &ok);
                 if (!ok) break;
                 mark_phase(4);
-                const uint32_t Suse = min(S, (uint32_t)kSurvCap);
-                // the next window starts after the kSurvCap-th survivor when
-                // the window is cut (generator order is rank order)
+                // Jobs whose survivor target is below the rows of a
+                // whole-window matrix decide their windows from one (unless a
+                // pair list does).  Such a window is cut after as many
+                // survivors as the matrix takes, any other after kSurvCap; the
+                // rest of its ranks start the next window.  (Jobs with larger
+                // targets, the sweeps of 2^28 or more candidates, measured
+                // slower with a matrix of their first survivors only.)
+                const bool dense_job = a.dense_rows != 0u && job.target < a.dense_rows;
+                const uint32_t cut = (dense_job && a.dense_cut != 0u && !pairs_on)
+                                         ? a.dense_rows : (uint32_t)kSurvCap;
+                const uint32_t Suse = min(S, cut);
+                // the next window starts after the cut-th survivor when the
+                // window is cut (generator order is rank order)
                 if (tid == 0) {
                     uint64_t rn = R0 + span;
-                    if (S > (uint32_t)kSurvCap) {
+                    if (S > cut) {
                         int j = 0;
-                        while (j + 1 < nG && s.pref[j + 1] <= (uint32_t)kSurvCap - 1u) ++j;
+                        while (j + 1 < nG && s.pref[j + 1] <= cut - 1u) ++j;
                         rn = R0 + ld_cg(grp.seg_off + ((size_t)par * G + j) * kChunk +
-                                        ((uint32_t)kSurvCap - 1u - s.pref[j])) + 1;
+                                        (cut - 1u - s.pref[j])) + 1;
                     }
                     s.bs.bcast64 = rn;
                 }
@@ -626,6 +644,33 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                                        ((unsigned long long)wseq << 32) |
                                            (np > kPairCap ? kPairCap + 1u : np));
                     }
+                    mark_phase(6);
+                }
+                // A window of more survivors than one conflict matrix takes
+                // is decided from the conflict matrix of its first Pd entries
+                // (all of them unless GC_DENSE_CUT=0), which the generators
+                // build: each gathers those entries and writes the rows of its
+                // share of the 4-row quads, then publishes with its pair flag.
+                const uint32_t Pd = (dense_job && !by_pairs && Suse > a.resolve_block)
+                                        ? min(Suse, a.dense_rows) : 0u;
+                if (lb > 0 && Pd > 0u) {
+                    for (int g = warp; g < nG; g += kWarps) {
+                        const uint32_t p0 = s.pref[g];
+                        if (p0 >= Pd) continue;
+                        const uint32_t cnt = min(s.pref[g + 1] - p0, Pd - p0);
+                        const Word* gx = seg_x + ((size_t)par * G + g) * kChunk;
+                        for (uint32_t i = lane; i < cnt; i += 32) s.list_x[p0 + i] = ld_cg(gx + i);
+                    }
+                    __syncthreads();
+                    mark_phase(5);
+                    if constexpr (!kWide)
+                        dense_build(s.list_x, Pd, d, grp.densebuf + (size_t)par * kDenseTriMax,
+                                    (uint32_t)gi + (uint32_t)nG * (uint32_t)warp,
+                                    (uint32_t)nG * (uint32_t)kWarps, my_tests);
+                    __threadfence();
+                    __syncthreads();
+                    if (tid == 0)
+                        st_release_u64(eflag + (size_t)par * G + gi, (unsigned long long)wseq << 32);
                     mark_phase(6);
                 }
                 if (lb == 0) {
@@ -680,6 +725,37 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                         } else {
                             ++pair_failed;
                         }
+                    }
+                    if (Pd > 0u) {
+                        await_counts(s, eflag + (size_t)par * G, nG, wseq, a.err,
+                                     a.timeout_cycles, &ok);
+                        if (!ok) break;
+                        mark_phase(4);
+                        uint32_t* T = &s.M[0][0];  // runs on into the code cache
+                        const uint4* src = reinterpret_cast<const uint4*>(
+                            grp.densebuf + (size_t)par * kDenseTriMax);
+                        const uint32_t nq = (dense_tri_words(Pd) + 3u) / 4u;
+                        for (uint32_t q = tid; q < nq; q += kBlock)
+                            reinterpret_cast<uint4*>(T)[q] = __ldcg(src + q);
+                        __syncthreads();
+                        if constexpr (!kWide) {
+                            nacc = dense_resolve(s.bs, s.dund, s.dacc, s.list_x, s.list_off, Pd,
+                                                 T, cur, s.acc_off,
+                                                 timing ? s.phase + 8 : nullptr);
+                            if (Suse > Pd) {
+                                // the rest: drop what the accepts exclude, then
+                                // the conflict matrices
+                                const uint32_t left = block_filter<false>(
+                                    s.bs, s.list_x + Pd, s.list_off + Pd, s.dead, Suse - Pd, cur,
+                                    0u, nacc, d, rt);
+                                if (left > 0u)
+                                    nacc = block_resolve<false>(
+                                        s.bs, s.list_x + Pd, s.list_off + Pd, s.dead, left, d,
+                                        cur, s.acc_off, s.M, rt,
+                                        timing ? s.phase + 8 : nullptr, a.resolve_block, nacc);
+                            }
+                        }
+                        decided = true;
                     }
                     if (!decided) nacc = resolve(Suse, rt);
                     resolve_tests += rt;
@@ -1095,19 +1171,53 @@ static bool dynamic_enabled() {
 }
 
 // Pipelined bitmap jobs, per group of G CTAs: flags [4G + 1] u64, the
-// accepts [2][kSurvCap] u32, the conflicting pairs [2][G][kPairCap] u32.
+// accepts [2][kSurvCap] u32, the whole-window conflict matrices
+// [2][kDenseTriMax] u32, the conflicting pairs [2][G][kPairCap] u32.
 static size_t pipe_flag_bytes(int G) {
     return align_up(sizeof(unsigned long long) * (4 * (size_t)G + 1));
 }
 static size_t pipe_bytes(int G) {
     return pipe_flag_bytes(G) + align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap) +
+           align_up(sizeof(uint32_t) * 2 * (size_t)kDenseTriMax) +
            align_up(sizeof(uint32_t) * 2 * (size_t)G * kPairCap);
 }
 static void set_pipe(GroupDesc& D, uint8_t* base) {
+    uint8_t* at = base + pipe_flag_bytes(D.ncta);
     D.pflags = reinterpret_cast<unsigned long long*>(base);
-    D.accbuf = reinterpret_cast<uint32_t*>(base + pipe_flag_bytes(D.ncta));
-    D.pairbuf = reinterpret_cast<uint32_t*>(base + pipe_flag_bytes(D.ncta) +
-                                            align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap));
+    D.accbuf = reinterpret_cast<uint32_t*>(at);
+    at += align_up(sizeof(uint32_t) * 2 * (size_t)kSurvCap);
+    D.densebuf = reinterpret_cast<uint32_t*>(at);
+    at += align_up(sizeof(uint32_t) * 2 * (size_t)kDenseTriMax);
+    D.pairbuf = reinterpret_cast<uint32_t*>(at);
+}
+
+// GC_PIPELINE=0 runs bitmap jobs with the sequential window loop (for
+// measurements); pipelining is on by default.
+static bool pipeline_enabled() {
+    const char* e = std::getenv("GC_PIPELINE");
+    return !(e && std::strcmp(e, "0") == 0);
+}
+
+// Pipelined windows of more survivors than one conflict matrix takes are
+// decided from a whole-window matrix that the generators build (GC_DENSE=0
+// turns this off, for measurements).  Its rows are limited by the resolver's
+// shared memory: the matrix area plus the code cache behind it.
+static bool dense_enabled() {
+    const char* e = std::getenv("GC_DENSE");
+    return !(e && std::strcmp(e, "0") == 0);
+}
+// GC_DENSE_CUT=0 keeps windows whole (up to kSurvCap survivors) and decides
+// the survivors beyond the matrix with the blocked matrices (measurements).
+static uint32_t dense_cut_mode() {
+    const char* e = std::getenv("GC_DENSE_CUT");
+    return (e && std::strcmp(e, "0") == 0) ? 0u : 1u;
+}
+static uint32_t dense_rows_for(uint32_t cache_words) {
+    if (!dense_enabled()) return 0u;
+    const uint64_t room = (uint64_t)kResolveWords * kResolveBlock + cache_words;
+    uint32_t P = kDenseMaxRows;
+    while (P > 0 && dense_tri_words(P) > room) P -= 32;
+    return P >= 128 ? P : 0u;
 }
 
 static Order make_order_host(const HostProblem& p) { return order_of(p, p.filter, p.orth); }
@@ -1178,6 +1288,18 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
             need_cache = std::max<uint64_t>(need_cache, jobs[j].p.bound);
     uint64_t room = (((size_t)optin - base) / wbytes) & ~(uint64_t)31;
     uint32_t cache = (uint32_t)std::min<uint64_t>(room, (need_cache + 31) & ~(uint64_t)31);
+    // pipelined bitmap jobs that decide windows from whole-window matrices
+    // (survivor target below the matrix's rows) hold them in the cache area
+    // too.  Only then: a larger shared-memory carve-out leaves less L1 for
+    // the kernel's spills (sweeps of n = 32 ran up to 1.4x slower with it).
+    const uint32_t dense_rows_max = dense_rows_for((uint32_t)room);
+    for (int j = 0; j < njobs; ++j) {
+        const BatchJob& J = jobs[j];
+        const uint32_t tgt = J.plan.survivor_target ? J.plan.survivor_target
+                                                    : default_target(J.plan.strategy, J.p);
+        if (J.plan.strategy == GC_STRATEGY_BITMAP && pipeline_enabled() && tgt < dense_rows_max)
+            cache = (uint32_t)room;
+    }
     L->cache_words = cache;
     L->smem_bytes = base + (size_t)cache * wbytes;
     std::vector<double> cost(njobs);
@@ -1187,15 +1309,26 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
     std::vector<std::vector<int>> per(ng);
     if (ng == njobs && ng > 1) {
         // one job per group: CTAs in proportion to the job's estimated work,
-        // at least kMinGroup (or an equal share if the SMs are too few)
+        // at least kMinGroup (or an equal share if the SMs are too few);
+        // distance jobs weigh 1.5x their estimate: the bitmap jobs' time is
+        // mostly their resolver's chain, which more CTAs do not shorten (the
+        // five codes of n = 24, d = 8 and n = 20, d = 4: 2.445 ms per launch
+        // with 1x, 2.409 with 1.5x, 2.413 with 2x, 2.581 with 3x);
+        // GC_DIST_SHARE overrides it (measurements)
         const int minc = std::max(1, std::min(kMinGroup, grid / ng));
+        double dist_share = 1.5;
+        if (const char* e = std::getenv("GC_DIST_SHARE")) dist_share = std::atof(e);
+        if (!(dist_share > 0.0 && dist_share < 100.0)) dist_share = 1.5;
+        std::vector<double> share(cost);
+        for (int j = 0; j < njobs; ++j)
+            if (jobs[j].plan.strategy == GC_STRATEGY_DISTANCE) share[j] *= dist_share;
         double total = 0;
-        for (double c : cost) total += c;
+        for (double c : share) total += c;
         int left = grid - minc * ng;
         std::vector<int> extra(ng, 0);
         int given = 0;
         for (int g = 0; g < ng; ++g) {
-            extra[g] = (int)std::floor(left * cost[g] / std::max(total, 1e-30));
+            extra[g] = (int)std::floor(left * share[g] / std::max(total, 1e-30));
             given += extra[g];
         }
         for (int g = 0; given < left; g = (g + 1) % ng, ++given) extra[g] += 1;
@@ -1306,8 +1439,6 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
 // Host-side fault injection for tests of the failure path: GC_FAULT=wait
 // makes group 0 wait for one CTA that does not exist, with a 0.2 s limit, so
 // its bounded waits expire and every job reports GC_ERR_TIMEOUT.
-// GC_PIPELINE=0 runs bitmap jobs with the sequential window loop (for
-// measurements); pipelining is on by default.
 // Pipelined windows: the generators list the window's conflicting pairs for
 // the resolver when that pays; GC_PAIRS=0 turns it off, GC_PAIRS=2 makes it
 // unconditional (measurements, tests).
@@ -1322,11 +1453,6 @@ static uint32_t pairs_mode() {
 static uint32_t timing_cta() {
     const char* e = std::getenv("GC_TIMING_CTA");
     return e ? (uint32_t)std::atoi(e) : 0u;
-}
-
-static bool pipeline_enabled() {
-    const char* e = std::getenv("GC_PIPELINE");
-    return !(e && std::strcmp(e, "0") == 0);
 }
 
 static bool inject_wait_fault() {
@@ -1388,6 +1514,7 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
         G.pflags = nullptr;
         G.accbuf = nullptr;
         G.pairbuf = nullptr;
+        G.densebuf = nullptr;
         if (L.g_pipe[g]) set_pipe(G, ws + L.g_pipe[g]);
     }
     cudaError_t e;
@@ -1464,6 +1591,8 @@ int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stre
     a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
     a.resolve_block = resolve_block_size();
     a.pairs = pairs_mode();
+    a.dense_rows = dense_rows_for(L.cache_words);
+    a.dense_cut = dense_cut_mode();
     a.timing_cta = timing_cta();
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel(kernel, dim3(L.grid), dim3(kBlock), args, L.smem_bytes,
@@ -1670,6 +1799,8 @@ int launch_server(ServeLayout& L, void* workspace, JobDesc* ring, unsigned* tail
     a.timeout_cycles = 20000000000ll;
     a.resolve_block = resolve_block_size();
     a.pairs = pairs_mode();
+    a.dense_rows = dense_rows_for(L.cache_words);
+    a.dense_cut = dense_cut_mode();
     a.timing_cta = timing_cta();
     int dev = 0, clk_khz = 0;
     cudaGetDevice(&dev);
