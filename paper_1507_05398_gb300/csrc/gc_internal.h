@@ -126,7 +126,9 @@ struct BatchLayout {
     int grid = 0, ngroups = 0;
     bool wide = false;          // the uint64-word kernel
     bool dynamic = false;       // groups claim jobs (longest first) as they free up
-    uint32_t cache_words = 0;   // shared-memory code cache (distance jobs)
+    bool dense = false;         // pipelined windows may use whole-window matrices
+    uint32_t cache_words = 0;   // shared-memory code cache (distance jobs; whole-window
+                                // matrices when dense)
     size_t smem_bytes = 0;
     std::vector<int> first_cta, ncta, job_begin, job_end, job_order;
     size_t off_err = 0, off_jobs = 0, off_order = 0, off_groups = 0;

@@ -73,6 +73,11 @@ constexpr uint32_t kPairShared = 6144;
 // paces the pipeline, and the search lengthens it by more than the
 // resolver saves (measured on the n = 20, d = 4 codes in groups of ~30).
 constexpr int kPairMinGenerators = 64;
+// A batch launch uses whole-window conflict matrices only if one of its
+// groups has at least this many generators: the 512 mixed codes of
+// n = 14-24 on groups of 3 generators took 122 ms per batch with them and
+// 113 ms without.
+constexpr int kDenseMinGenerators = 8;
 constexpr int kMaxGroupCtas = 1024;
 constexpr int kMinGroup = 8;       // CTAs of the smallest group when sizes follow cost
 enum : int { kStratDistance = 1, kStratBitmap = 2 };
@@ -1288,18 +1293,6 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
             need_cache = std::max<uint64_t>(need_cache, jobs[j].p.bound);
     uint64_t room = (((size_t)optin - base) / wbytes) & ~(uint64_t)31;
     uint32_t cache = (uint32_t)std::min<uint64_t>(room, (need_cache + 31) & ~(uint64_t)31);
-    // pipelined bitmap jobs that decide windows from whole-window matrices
-    // (survivor target below the matrix's rows) hold them in the cache area
-    // too.  Only then: a larger shared-memory carve-out leaves less L1 for
-    // the kernel's spills (sweeps of n = 32 ran up to 1.4x slower with it).
-    const uint32_t dense_rows_max = dense_rows_for((uint32_t)room);
-    for (int j = 0; j < njobs; ++j) {
-        const BatchJob& J = jobs[j];
-        const uint32_t tgt = J.plan.survivor_target ? J.plan.survivor_target
-                                                    : default_target(J.plan.strategy, J.p);
-        if (J.plan.strategy == GC_STRATEGY_BITMAP && pipeline_enabled() && tgt < dense_rows_max)
-            cache = (uint32_t)room;
-    }
     L->cache_words = cache;
     L->smem_bytes = base + (size_t)cache * wbytes;
     std::vector<double> cost(njobs);
@@ -1378,6 +1371,29 @@ bool batch_layout(const BatchJob* jobs, int njobs, int ngroups_req, BatchLayout*
             for (int j : per[g]) L->job_order.push_back(j);
             L->job_end[g] = (int)L->job_order.size();
         }
+    }
+    // Pipelined bitmap jobs that decide windows from whole-window matrices
+    // (survivor target below the matrix's rows, a group of at least
+    // kDenseMinGenerators + 1 CTAs) hold them in the cache area too.  Only
+    // then: a larger shared-memory carve-out leaves less L1 for the kernel's
+    // spills (sweeps of n = 32 ran up to 1.4x slower with it).
+    const uint32_t dense_rows_max = dense_rows_for((uint32_t)room);
+    bool dense_any = false;
+    for (int g = 0; g < ng && pipeline_enabled(); ++g) {
+        if (L->ncta[g] - 1 < kDenseMinGenerators) continue;
+        const int q0 = L->dynamic ? 0 : L->job_begin[g], q1 = L->dynamic ? njobs : L->job_end[g];
+        for (int q = q0; q < q1; ++q) {
+            const BatchJob& J = jobs[L->job_order[q]];
+            const uint32_t tgt = J.plan.survivor_target ? J.plan.survivor_target
+                                                        : default_target(J.plan.strategy, J.p);
+            dense_any |= J.plan.strategy == GC_STRATEGY_BITMAP && tgt < dense_rows_max;
+        }
+    }
+    L->dense = dense_any;
+    if (dense_any) {
+        cache = (uint32_t)room;
+        L->cache_words = cache;
+        L->smem_bytes = base + (size_t)cache * wbytes;
     }
     // workspace
     size_t off = 0;
@@ -1591,7 +1607,7 @@ int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stre
     a.timeout_cycles = inject_wait ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
     a.resolve_block = resolve_block_size();
     a.pairs = pairs_mode();
-    a.dense_rows = dense_rows_for(L.cache_words);
+    a.dense_rows = L.dense ? dense_rows_for(L.cache_words) : 0u;
     a.dense_cut = dense_cut_mode();
     a.timing_cta = timing_cta();
     void* args[] = {&a};
