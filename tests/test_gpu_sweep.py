@@ -168,6 +168,25 @@ def test_generator_pair_lists(case, monkeypatch):
             assert st.pair_windows > 0
 
 
+@pytest.mark.parametrize("mode", [("1", "1"), ("1", "0"), ("0", "1")],
+                         ids=["whole-window", "whole-window-tail", "blocked"])
+@pytest.mark.parametrize("o", ORDERS)
+def test_whole_window_matrices(o, mode, monkeypatch):
+    """n = 20, d = 4 bitmap codes on the whole GPU: a pipelined window of more
+    survivors than one conflict matrix takes is decided from the whole
+    window's conflict matrix, which the generator CTAs build, and is cut
+    after as many survivors as that matrix holds.  GC_DENSE_CUT=0 keeps the
+    windows whole and sends the survivors beyond the matrix to the blocked
+    matrices; GC_DENSE=0 uses the blocked matrices only.  The code is the
+    oracle's in every mode."""
+    dense, cut = mode
+    monkeypatch.setenv("GC_DENSE", dense)
+    monkeypatch.setenv("GC_DENSE_CUT", cut)
+    got, st = gpu_code(20, 4, o, -1, "bitmap")
+    assert got.tolist() == oracle.greedy_ball(20, 4, o).tolist(), (o, mode)
+    assert st.codewords == len(got)
+
+
 def test_pair_list_overflow_falls_back_to_matrices(monkeypatch):
     """GC_PAIRS=2 on n = 20, d = 4 grevlex (windows with thousands of
     conflicting pairs): some windows are decided from the lists, the rest
