@@ -1,6 +1,8 @@
 // gc_block.cuh -- CTA-wide primitives of the sweep: order-preserving
 // compaction, the candidate-vs-codeword distance test (warp-level scan and
-// the CTA-wide 2-D tiling of it), and the in-order resolver.  Functions
+// the CTA-wide 2-D tiling of it), and the in-order resolvers (blocked
+// conflict matrices, a whole-window matrix, a list of conflicting pairs,
+// bucketed conflict search).  Functions
 // documented as CTA-wide are called by every thread of a CTA of kBlock
 // threads (they contain __syncthreads).  Every primitive takes vectors of
 // either width: W = uint32_t (n <= 32) or uint64_t (n <= 64).

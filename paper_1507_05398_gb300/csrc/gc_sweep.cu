@@ -27,7 +27,7 @@
 //     Every CTA keeps its own copy of the accepts, so no second wait is needed.
 // The window size adapts so that about `target` candidates survive step 1; if
 // more than kSurvCap survive, the window is cut after the kSurvCap-th one.
-// Two refinements of this scheme:
+// Refinements of this scheme:
 //  - distance jobs with a long code deal the window out in kSlice-rank
 //    slices round-robin instead of one chunk per CTA, because the test cost
 //    per candidate is very uneven along the order;
@@ -36,7 +36,12 @@
 //  - in pipelined groups of 64 or more generators, after a window that
 //    accepted at least 7/8 of its survivors, the generators also list the
 //    next window's conflicting pairs between them, and the resolver decides
-//    it in rounds over that list (pair_resolve) instead of conflict matrices.
+//    it in rounds over that list (pair_resolve) instead of conflict matrices;
+//  - otherwise, pipelined jobs of small survivor targets (in launches with
+//    a group of kDenseMinGenerators or more generators) have the generators
+//    build the window's whole conflict matrix, which the resolver copies
+//    into shared memory and decides in rounds (dense_build, dense_resolve);
+//    such windows are cut after as many survivors as the matrix holds.
 // The kernel is instantiated for narrow vectors (uint32 words, n <= 32, both
 // strategies) and wide ones (uint64 words, n <= 64, distance strategy only).
 #include <algorithm>
