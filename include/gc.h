@@ -72,7 +72,7 @@ enum {
     GC_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     GC_ERR_OOM = 4,         /* device or host allocation failed */
     GC_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
-    GC_ERR_UNSUPPORTED = 6, /* valid request this build does not handle */
+    GC_ERR_UNSUPPORTED = 6, /* valid request the library does not handle */
     GC_ERR_INTERNAL = 7     /* an internal consistency check failed */
 };
 
