@@ -80,8 +80,18 @@ enum {
 typedef enum {
     GC_STRATEGY_AUTO = 0,
     GC_STRATEGY_DISTANCE = 1, /* test each candidate against the code */
-    GC_STRATEGY_BITMAP = 2    /* exclusion bitmap of radius-(d-1) balls */
+    GC_STRATEGY_BITMAP = 2,   /* exclusion bitmap of radius-(d-1) balls */
+    /* The same exclusion bitmap, with every SM taking part in every window
+     * of the one code (lockstep windows separated by grid-wide barriers;
+     * no resolver pipeline).  gc_plan() picks it for bitmap problems of at
+     * least 2^GC_GRID_MIN_LOG2 candidates; a batch or a server runs such a
+     * job as GC_STRATEGY_BITMAP.  n <= 32, no orthogonality constraint. */
+    GC_STRATEGY_BITMAP_GRID = 3
 } gc_strategy;
+
+/* Smallest rank space (log2) for which gc_plan() runs a bitmap problem with
+ * GC_STRATEGY_BITMAP_GRID. */
+#define GC_GRID_MIN_LOG2 26
 
 /* Extra constraints on the greedy. */
 enum {
@@ -114,7 +124,8 @@ typedef struct {
     uint32_t survivor_target; /* window sizing aims at this many survivors
                                  (gc_plan: 512 distance, 1024 bitmap; 4096
                                  lex/Gray and 2048 graded for bitmap sweeps
-                                 of >= 2^28 candidates) */
+                                 of >= 2^28 candidates; 4400 for the grid
+                                 strategy, whose windows end after 4096) */
 } gc_plan_t;
 
 /* Counters filled by the sweep (device-side writes, read after sync). */

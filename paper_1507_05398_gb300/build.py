@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgc.so")
-SOURCES = ["gc_sweep.cu", "gc_steps.cu", "gc_capi.cu", "gc_probe.cu", "gc_noalloc.cu", "gc_server.cu", "gc_tune.cu"]
+SOURCES = ["gc_sweep.cu", "gc_steps.cu", "gc_capi.cu", "gc_probe.cu", "gc_noalloc.cu", "gc_server.cu", "gc_tune.cu",
+           "gc_gridsweep.cu"]
 HEADERS = ["gc_device.cuh", "gc_block.cuh", "gc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

@@ -175,10 +175,14 @@ void plan_for(const HostProblem& p, gc_plan_t* pl) {
         pl->strategy = GC_STRATEGY_BITMAP;
     else
         pl->strategy = GC_STRATEGY_DISTANCE;
+    // a large bitmap sweep of one code runs on every SM in lockstep windows
+    if (pl->strategy == GC_STRATEGY_BITMAP && p.valid >= (1ull << GC_GRID_MIN_LOG2))
+        pl->strategy = GC_STRATEGY_BITMAP_GRID;
     pl->survivor_target = default_target(pl->strategy, p);
     if (const char* e = std::getenv("GC_STRATEGY")) {
         if (!std::strcmp(e, "distance")) pl->strategy = GC_STRATEGY_DISTANCE;
         if (!std::strcmp(e, "bitmap")) pl->strategy = GC_STRATEGY_BITMAP;
+        if (!std::strcmp(e, "grid")) pl->strategy = GC_STRATEGY_BITMAP_GRID;
         pl->survivor_target = default_target(pl->strategy, p);
     }
 }
@@ -195,15 +199,17 @@ static bool resolve_plan(const HostProblem& p, const gc_plan_t* in, gc_plan_t* o
         if (in->window_max) out->window_max = in->window_max;
         if (in->survivor_target) out->survivor_target = in->survivor_target;
     }
-    return out->strategy == GC_STRATEGY_DISTANCE || out->strategy == GC_STRATEGY_BITMAP;
+    return out->strategy == GC_STRATEGY_DISTANCE || out->strategy == GC_STRATEGY_BITMAP ||
+           out->strategy == GC_STRATEGY_BITMAP_GRID;
 }
 
 // The plan of a wide sweep: the distance strategy (the bitmap has no wide
 // form); an explicit bitmap request fails.
 static bool resolve_plan_wide(const HostProblem& p, const gc_plan_t* in, gc_plan_t* out) {
     if (!resolve_plan(p, in, out)) return false;
-    if (out->strategy == GC_STRATEGY_BITMAP) {
-        if (in && in->strategy == GC_STRATEGY_BITMAP) return false;
+    if (out->strategy == GC_STRATEGY_BITMAP || out->strategy == GC_STRATEGY_BITMAP_GRID) {
+        if (in && (in->strategy == GC_STRATEGY_BITMAP || in->strategy == GC_STRATEGY_BITMAP_GRID))
+            return false;
         out->strategy = GC_STRATEGY_DISTANCE;
         out->survivor_target =
             (in && in->survivor_target) ? in->survivor_target : kTargetDistance;
@@ -247,9 +253,18 @@ static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, void
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? GC_OK : fail(GC_ERR_CUDA, cudaGetErrorString(e));
     }
+    std::string why;
+    if (plan.strategy == GC_STRATEGY_BITMAP_GRID && !wide) {
+        GridLayout GL;
+        if (!grid_sweep_layout(p, plan, &GL, &why)) return fail(GC_ERR_UNSUPPORTED, why);
+        if (ws_bytes < GL.total) return fail(GC_ERR_INVALID, "workspace too small");
+        if (((uintptr_t)ws & 255u) != 0) return fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
+        const int rc = launch_grid_sweep(p, GL, static_cast<uint32_t*>(d_out), capacity, d_stats,
+                                         ws, s, &why);
+        return rc ? fail(rc, why) : GC_OK;
+    }
     BatchJob job{p, plan, d_out, capacity, d_stats, wide};
     BatchLayout L;
-    std::string why;
     if (!batch_layout(&job, 1, 1, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
     if (ws_bytes < L.total) return fail(GC_ERR_INVALID, "workspace too small");
     if (((uintptr_t)ws & 255u) != 0) return fail(GC_ERR_INVALID, "workspace not 256-byte aligned");
@@ -261,6 +276,10 @@ static int generate_async_impl(const HostProblem& p, const gc_plan_t& plan, void
 static size_t single_workspace(const HostProblem& p, const gc_plan_t& pl, std::string* why,
                                bool wide = false) {
     if (p.d <= 1 && !p.filter && !p.orth && !wide) return 256;
+    if (pl.strategy == GC_STRATEGY_BITMAP_GRID && !wide) {
+        GridLayout GL;
+        return grid_sweep_layout(p, pl, &GL, why) ? GL.total : 0;
+    }
     BatchJob job{p, pl, nullptr, 0, nullptr, wide};
     BatchLayout L;
     if (!batch_layout(&job, 1, 1, &L, why)) return 0;
@@ -281,6 +300,7 @@ static int make_batch(const gc_job* jobs, int njobs, std::vector<BatchJob>* out)
         in.strategy = J.strategy;
         if (!resolve_plan(B.p, &in, &B.plan))
             return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": bad strategy");
+        B.plan.strategy = batch_strategy(B.plan.strategy);
         if (!J.d_stats || (!J.d_out && J.capacity > 0))
             return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": null pointer");
         B.d_out = J.d_out;

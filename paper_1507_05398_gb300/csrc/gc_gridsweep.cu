@@ -1,0 +1,712 @@
+// gc_gridsweep.cu -- the exclusion-bitmap sweep of one code on the whole
+// GPU in lockstep windows (the "grid" bitmap strategy).
+//
+// It computes what the pipelined bitmap sweep of gc_sweep.cu computes -- the
+// ordered greedy code of Section 4 -- for one code at a time, with every SM
+// taking part in every step of every window.  Window t of W consecutive
+// ranks takes two phases, each ended by a grid-wide barrier (one arrival
+// counter, polled by one thread per CTA):
+//  A. every CTA ORs its share of the balls of window t-1's accepts into the
+//     exclusion bitmap and writes its share of them to the output, then
+//     generates its contiguous chunk of window t from the ranks (Section 4.2
+//     orders, closed form) and drops the candidates whose bit is set.  The
+//     bitmap then holds the radius-(d-1) balls of every codeword accepted in
+//     windows t-2 and earlier (marked before the last barrier) and whatever
+//     of window t-1's has landed.  The survivors go to the CTA's segment, in
+//     rank order.
+//  B. every CTA gathers the window's survivors (the first kGwSurvCap; the
+//     window is cut after them) and tests its rows (entries i = CTA index
+//     mod grid) against window t-1's accepts, which every CTA holds in
+//     shared memory -- a hit rejects the entry -- and against every earlier
+//     entry of the window, listing the conflicting pairs (Hamming distance
+//     < d) of the entries no accept rejected.  A thread takes columns (one
+//     accept or one entry) and tests them against all the CTA's rows, so
+//     every warp has the same work and each loaded word serves every row.
+// Then every CTA, from the same data, decides the window exactly as the
+// serial loop would: with no pair, the entries no accept rejected are the
+// accepts; otherwise rounds over the pair list (an entry is rejected once an
+// earlier neighbour is accepted and accepted once every earlier neighbour is
+// rejected); when the list is too long, the conflict matrices of
+// block_resolve.  Every CTA keeps the accepts for the next window.
+// Compared with the pipelined form, no CTA waits on another's flag word
+// (the flag all-gathers of that design took several microseconds each at
+// 152 CTAs, the counter barrier about two), nothing runs on one SM while the
+// others wait, and the test against the previous window's accepts, the pair
+// search and the marks are spread over every SM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "gc_block.cuh"
+#include "gc_internal.h"
+
+namespace gc {
+
+constexpr int kGwSurvCap = 4096;        // survivors decided per window
+constexpr int kGwChunk = 4096;          // candidates per CTA per window
+constexpr uint32_t kGwPairCap = 2048;   // pairs one CTA may list per window
+constexpr uint32_t kGwPairSmem = 16384; // pairs a CTA takes into shared memory
+constexpr int kGwMaxCtas = kBlock;      // one count per thread in the prefix scans
+static_assert(kGwSurvCap <= 65536, "pairs pack two entry indices in 16 bits each");
+static_assert(kGwSurvCap == 4 * kBlock, "the accept compaction gives a thread four entries");
+static_assert(kGwPairCap <= kGwPairSmem, "a CTA's own pairs are staged in the pair area");
+
+struct GwArgs {
+    Order ord;
+    int d;
+    uint32_t* out;
+    uint64_t cap;
+    gc_stats* stats;
+    const uint32_t* hball;    // word-grouped ball table (high_ball_kernel)
+    uint32_t hball_len;
+    uint32_t* bitmap;         // 2^n bits, vector-indexed
+    uint32_t* seg_x;          // [2][grid][kGwChunk] survivors of each CTA's chunk
+    uint32_t* seg_off;        // [2][grid][kGwChunk] their offsets from the window start
+    uint32_t* slot;           // [2][grid] survivor counts
+    uint32_t* pslot;          // [2][grid] pair counts (kGwPairCap + 1: overflow)
+    uint32_t* pairbuf;        // [grid][kGwPairCap] (earlier << 16) | later
+    uint8_t* killbuf;         // [kGwSurvCap] 1: the entry meets a previous accept
+    unsigned* ctrl;           // [0] barrier arrivals, [1] error word
+    uint32_t wmin, wmax, target;
+    long long timeout_cycles;
+    uint32_t timing_cta;
+    uint32_t extra_arrivals;  // fault injection: barriers wait for this many CTAs more
+    uint32_t reversed;        // 1: the bitmap is indexed by the bit-reversed vector
+};
+
+struct __align__(16) GwSmem {
+    uint32_t C[kMaxN + 1][kMaxN + 1];
+    uint32_t lowball[8][32];  // lowball[r][c]: bits y < 32 with popc(y ^ c) <= r
+    uint32_t lowlight[8];     // lowlight[k]: bits y < 32 with popc(y) < k
+    uint32_t pref[kGwMaxCtas + 1];
+    __align__(16) uint32_t wx[kGwSurvCap];      // own chunk (A), the window (B)
+    __align__(16) uint32_t woff[kGwSurvCap];
+    __align__(16) uint32_t ax[kGwSurvCap];      // the previous window's accepts
+    __align__(16) uint32_t ax_off[kGwSurvCap];  // and their ranks (n <= 32)
+    __align__(16) uint32_t acc[kGwSurvCap];     // block_resolve's output
+    __align__(16) uint32_t acc_off[kGwSurvCap];
+    uint8_t state[kGwSurvCap];                  // 0 undecided, 1 accepted, 2 rejected
+    uint8_t flags[2 * kGwSurvCap];              // row kills (B); killed / blocked (rounds)
+    BlockScratch bs;
+    unsigned long long phase[12];
+    long long tprev;
+    uint32_t npairs;
+    uint32_t fine;
+    union {
+        uint32_t pairs[kGwPairSmem];
+        uint32_t M[kResolveWords][kResolveBlock];
+    } u;
+};
+
+// CTA-wide grid barrier: one arrival per CTA on a counter that only grows;
+// the barrier of epoch e is passed once it reaches (e + 1) * arrivals.
+// Bounded: on a timeout (or an error another CTA reported) returns false.
+__device__ bool gw_sync(GwSmem& s, const GwArgs& a, uint32_t& epoch) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.ctrl, 1u);
+        const unsigned target = (epoch + 1u) * (gridDim.x + a.extra_arrivals);
+        const long long t0 = clock64();
+        uint32_t fine = 1u;
+        for (;;) {
+            if ((int)(ld_acquire_gpu(a.ctrl) - target) >= 0) break;
+            if (ld_acquire_gpu(a.ctrl + 1) != 0u) { fine = 0u; break; }
+            if (clock64() - t0 > a.timeout_cycles) {
+                atomicExch(a.ctrl + 1, 1u);
+                fine = 0u;
+                break;
+            }
+        }
+        __threadfence();
+        s.fine = fine;
+    }
+    ++epoch;
+    __syncthreads();
+    return s.fine != 0u;
+}
+
+// CTA-wide.  The window's decisions from its pair list: on entry state[i]
+// is 2 for entries already rejected (they meet a previous window's accept)
+// and 0 for the rest; pairs[0..P) hold (k << 16) | i for conflicting pairs
+// k < i.  Each round decides every undecided entry whose earlier neighbours
+// are all decided (the first undecided entry always is, so the rounds end);
+// then the accepts x[i] and their ranks R0 + off[i] are appended in order to
+// ax/ax_off.  Returns how many; counts rounds in *rounds.
+__device__ uint32_t gw_pair_rounds(GwSmem& s, uint32_t n, uint32_t P, uint64_t R0,
+                                   uint64_t* rounds) {
+    uint8_t* killed = s.flags;
+    uint8_t* blocked = s.flags + kGwSurvCap;
+    const int lane = lane_id();
+    for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
+        killed[i] = 0;
+        blocked[i] = 0;
+    }
+    if (threadIdx.x < 3) s.bs.left[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t round = 0;; ++round) {
+        ++*rounds;
+        const uint32_t slot = round % 3u, next = (round + 1u) % 3u;
+        if (threadIdx.x == 0) s.bs.left[next] = 0u;
+        for (uint32_t e = threadIdx.x; e < P; e += kBlock) {
+            const uint32_t pr = s.u.pairs[e];
+            const uint32_t k = pr >> 16, i = pr & 0xffffu;
+            if (s.state[i] == 0) {
+                const uint8_t sk = s.state[k];
+                if (sk == 1) killed[i] = 1;
+                else if (sk == 0) blocked[i] = 1;
+            }
+        }
+        __syncthreads();
+        bool left = false;
+        for (uint32_t i = threadIdx.x; i < n; i += kBlock)
+            if (s.state[i] == 0) {
+                if (killed[i]) s.state[i] = 2;
+                else if (!blocked[i]) s.state[i] = 1;
+                else left = true;
+                killed[i] = 0;
+                blocked[i] = 0;
+            }
+        if (__any_sync(kFull, left) && lane == 0) s.bs.left[slot] = 1u;
+        __syncthreads();
+        if (s.bs.left[slot] == 0u) break;
+    }
+    uint32_t nacc = 0;
+    for (uint32_t t0 = 0; t0 < n; t0 += kBlock) {
+        const uint32_t i = t0 + threadIdx.x;
+        const bool keep = i < n && s.state[i] == 1;
+        nacc = block_append(s.bs, keep, keep ? s.wx[i] : 0u,
+                            keep ? (uint32_t)(R0 + s.woff[i]) : 0u, s.ax, s.ax_off, nacc);
+    }
+    return nacc;
+}
+
+__global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_constant__ GwArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    GwSmem& s = *reinterpret_cast<GwSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = lane_id();
+    const uint32_t G = gridDim.x, lb = blockIdx.x;
+    const Order& o = a.ord;
+    const int n = o.n, d = a.d;
+    for (int q = tid; q < (kMaxN + 1) * (kMaxN + 1); q += kBlock) {
+        const int p = q / (kMaxN + 1), k = q % (kMaxN + 1);
+        uint64_t r = (k <= p) ? 1u : 0u;
+        for (int i = 1; i <= k && k <= p; ++i) r = r * (uint64_t)(p - k + i) / (uint64_t)i;
+        s.C[p][k] = (uint32_t)r;
+    }
+    {
+        const int nl = n < 5 ? n : 5;
+        for (int q = tid; q < 8 * 32; q += kBlock) {
+            const int r = q / 32, c = q % 32;
+            uint32_t m = 0;
+            for (int y = 0; y < (1 << nl); ++y)
+                if (__popc((unsigned)(y ^ c)) <= r) m |= 1u << y;
+            s.lowball[r][c] = m;
+        }
+        for (int k = tid; k < 8; k += kBlock) {
+            uint32_t m = 0;
+            for (int y = 0; y < (1 << nl); ++y)
+                if (__popc((unsigned)y) < k) m |= 1u << y;
+            s.lowlight[k] = m;
+        }
+    }
+    const bool timing = lb == (a.timing_cta < G ? a.timing_cta : 0u) && tid == 0;
+    if (timing) {
+        for (int k = 0; k < 12; ++k) s.phase[k] = 0;
+        s.tprev = clock64();
+    }
+    auto mark_phase = [&](int k) {
+        if (timing) {
+            const long long t = clock64();
+            s.phase[k] += (unsigned long long)(t - s.tprev);
+            s.tprev = t;
+        }
+    };
+    if (lb == 0 && tid == 0) {
+        gc_stats* st = a.stats;
+        st->codewords = 0; st->candidates = 0; st->dense_tests = 0; st->executed_tests = 0;
+        st->marks = 0; st->windows = 0; st->survivors = 0; st->status = 0; st->strategy = 0;
+        for (int k = 0; k < 12; ++k) st->phase_cycles[k] = 0;
+        st->pair_windows = 0; st->pair_fallbacks = 0;
+    }
+    // clear this CTA's share of the bitmap
+    {
+        const uint64_t words = ((1ull << n) + 31) / 32;
+        const uint64_t per = (words + G - 1) / G;
+        const uint64_t w0 = min((uint64_t)lb * per, words), w1 = min(w0 + per, words);
+        for (uint64_t w = w0 + tid; w < w1; w += kBlock) a.bitmap[w] = 0u;
+    }
+    uint32_t epoch = 0;
+    bool ok = gw_sync(s, a, epoch);
+    mark_phase(4);
+
+    // ORs this CTA's share of the balls of ax[0..nacc) into the bitmap.  The
+    // (ball word, codeword) pairs are taken ball-word-major, so the lanes of
+    // a warp mark the same ball word around neighbouring codewords, which
+    // lie close together in the bitmap: consecutive lex, Gray and grlex
+    // codewords share their high bits, consecutive grevlex codewords their
+    // low bits, so the grevlex bitmap is indexed by the bit-reversed vector
+    // (a Hamming ball reversed is the ball around the reversed centre, and
+    // weights do not change).  Only vectors after the codeword in the order
+    // can still be candidates: lex and Gray skip the words wholly before it,
+    // the graded orders mask the lighter vectors.
+    uint64_t my_marks = 0;
+    auto mark_share = [&](uint32_t nacc) {
+        const uint32_t hl = a.hball_len;
+        if (nacc == 0 || hl == 0) return;
+        const uint64_t total = (uint64_t)nacc * hl;
+        const uint64_t per = (total + G - 1) / G;
+        const uint64_t q0 = min((uint64_t)lb * per, total), q1 = min(q0 + per, total);
+        const uint64_t qs = q0 + tid;
+        uint32_t j = (uint32_t)(qs / nacc), i = (uint32_t)(qs - (uint64_t)j * nacc);
+        const uint32_t dj = kBlock / nacc, di = kBlock - dj * nacc;
+        for (uint64_t q = qs; q < q1; q += kBlock) {
+            const uint32_t c = a.reversed ? reverse_n(s.ax[i], n) : s.ax[i];
+            const uint32_t e = __ldg(a.hball + j);
+            const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
+            uint32_t mask = s.lowball[e & 7u][c & 31u];
+            bool skip = false;
+            if (o.ord == kLex) {
+                skip = word < cw;
+                if (word == cw) mask &= ~((2u << (c & 31u)) - 1u);
+            } else if (o.ord == kGray) {
+                skip = gray_inverse(word) < gray_inverse(cw);
+            } else if (o.ord == kGrlex || o.ord == kGrevlex) {
+                const int below = __popc(c) - __popc(word);
+                if (below > 0) mask &= ~s.lowlight[below < 7 ? below : 7];
+            }
+            if (!skip && mask) {
+                atomicOr(a.bitmap + word, mask);
+                ++my_marks;
+            }
+            i += di;
+            j += dj;
+            if (i >= nacc) {
+                i -= nacc;
+                ++j;
+            }
+        }
+    };
+
+    uint64_t R0 = 0, K = 0, Kprev = 0;
+    uint32_t W = a.wmin, nprev = 0;
+    uint64_t my_tests = 0, dense = 0, windows = 0, surv_total = 0;
+    uint64_t pair_windows = 0, fallbacks = 0, rounds_total = 0;
+    // ax/ax_off[0..nprev): the accepts of the previous window, in every CTA;
+    // this CTA's share of them goes to the output
+    auto emit_prev = [&]() {
+        const uint32_t per = (nprev + G - 1) / G;
+        const uint32_t i0 = min(lb * per, nprev), i1 = min(i0 + per, nprev);
+        for (uint32_t i = i0 + tid; i < i1; i += kBlock) {
+            const uint64_t pos = Kprev + i;
+            if (pos < a.cap) a.out[pos] = s.ax[i];
+        }
+        if (lb == 0 && !o.filter)
+            for (uint32_t i = tid; i < nprev; i += kBlock) dense += o.N - 1 - s.ax_off[i];
+    };
+    uint32_t t = 0;
+    for (; ok && R0 < o.N; ++t) {
+        const int p = t & 1;
+        const uint64_t span = min((uint64_t)W, o.N - R0);
+        // ---- A: the previous window's marks and output; this CTA's chunk,
+        // filtered by the bitmap
+        mark_share(nprev);
+        emit_prev();
+        __syncthreads();
+        mark_phase(0);
+        {
+            const uint64_t chunk = (span + G - 1) / G;
+            const uint64_t c0 = min(R0 + (uint64_t)lb * chunk, R0 + span);
+            const uint64_t c1 = min(c0 + chunk, R0 + span);
+            uint32_t na = 0;
+            for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
+                const uint64_t r = t0 + tid;
+                uint32_t x = 0;
+                bool keep = false;
+                if (r < c1) {
+                    keep = unrank(o, s.C, r, x);
+                            if (keep) {
+                        const uint32_t key = a.reversed ? reverse_n(x, n) : x;
+                        keep = !((ld_cg(a.bitmap + (key >> 5)) >> (key & 31u)) & 1u);
+                    }
+                }
+                na = block_append(s.bs, keep, x, (uint32_t)(r - R0), s.wx, s.woff, na);
+            }
+            uint32_t* sx = a.seg_x + ((size_t)p * G + lb) * kGwChunk;
+            uint32_t* so = a.seg_off + ((size_t)p * G + lb) * kGwChunk;
+            for (uint32_t i = tid; i < na; i += kBlock) {
+                sx[i] = s.wx[i];
+                so[i] = s.woff[i];
+            }
+            if (tid == 0) a.slot[(size_t)p * G + lb] = na;
+        }
+        mark_phase(1);
+        ok = gw_sync(s, a, epoch);
+        if (!ok) break;
+        mark_phase(4);
+
+        // ---- B: gather the window, test this CTA's rows
+        uint32_t S = 0;
+        {
+            const uint32_t v = (uint32_t)tid < G ? ld_cg(a.slot + (size_t)p * G + tid) : 0u;
+            const uint32_t ex = block_exclusive_scan(s.bs, v, &S);
+            if ((uint32_t)tid < G) s.pref[tid] = ex;
+            if (tid == 0) s.pref[G] = S;
+            __syncthreads();
+        }
+        const uint32_t Suse = min(S, (uint32_t)kGwSurvCap);
+        if (tid == 0) {
+            uint64_t rn = R0 + span;
+            if (S > (uint32_t)kGwSurvCap) {
+                // the window ends after its kGwSurvCap-th survivor
+                uint32_t g = 0;
+                while (g + 1 < G && s.pref[g + 1] <= (uint32_t)kGwSurvCap - 1u) ++g;
+                rn = R0 + ld_cg(a.seg_off + ((size_t)p * G + g) * kGwChunk +
+                                ((uint32_t)kGwSurvCap - 1u - s.pref[g])) + 1;
+            }
+            s.bs.bcast64 = rn;
+            s.npairs = 0;
+        }
+        // entry e of the window sits in the segment of the last CTA g with
+        // pref[g] <= e (empty segments share their successor's prefix)
+        {
+            uint32_t at[kGwSurvCap / kBlock];  // < 2 * grid * kGwChunk
+#pragma unroll
+            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k) {
+                const uint32_t e = tid + k * kBlock;
+                uint32_t lo = 0, hi = G;
+                while (hi - lo > 1u) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s.pref[mid] <= e) lo = mid;
+                    else hi = mid;
+                }
+                at[k] = ((uint32_t)p * G + lo) * (uint32_t)kGwChunk + (e - s.pref[lo]);
+            }
+            uint32_t vx[kGwSurvCap / kBlock], vo[kGwSurvCap / kBlock];
+#pragma unroll
+            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k)
+                if (tid + k * kBlock < Suse) {
+                    vx[k] = ld_cg(a.seg_x + at[k]);
+                    vo[k] = ld_cg(a.seg_off + at[k]);
+                }
+#pragma unroll
+            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k)
+                if (tid + k * kBlock < Suse) {
+                    s.wx[tid + k * kBlock] = vx[k];
+                    s.woff[tid + k * kBlock] = vo[k];
+                }
+        }
+        // this CTA's rows: entries lb + r * G, r < rows; s.flags[r] = killed
+        const uint32_t rows = Suse > lb ? (Suse - lb + G - 1) / G : 0u;
+        for (uint32_t r = tid; r < rows; r += kBlock) s.flags[r] = 0;
+        __syncthreads();
+        const uint64_t Rnext = s.bs.bcast64;
+        mark_phase(5);
+        {
+            // the previous window's accepts against every row
+            for (uint32_t c = tid; c < nprev; c += kBlock) {
+                const uint32_t y = s.ax[c];
+                uint32_t r = 0;
+                for (; r + 4 <= rows; r += 4) {
+                    const uint32_t x0 = s.wx[lb + r * G], x1 = s.wx[lb + (r + 1) * G];
+                    const uint32_t x2 = s.wx[lb + (r + 2) * G], x3 = s.wx[lb + (r + 3) * G];
+                    if (popc(x0 ^ y) < d) s.flags[r] = 1;
+                    if (popc(x1 ^ y) < d) s.flags[r + 1] = 1;
+                    if (popc(x2 ^ y) < d) s.flags[r + 2] = 1;
+                    if (popc(x3 ^ y) < d) s.flags[r + 3] = 1;
+                }
+                for (; r < rows; ++r)
+                    if (popc(s.wx[lb + r * G] ^ y) < d) s.flags[r] = 1;
+                my_tests += rows;
+            }
+            // the window's entries against the later rows: pairs (k, i)
+            for (uint32_t k = tid; k < Suse; k += kBlock) {
+                const uint32_t y = s.wx[k];
+                const uint32_t r0 = k < lb ? 0u : (k - lb) / G + 1u;
+                for (uint32_t r = r0; r < rows; ++r) {
+                    const uint32_t i = lb + r * G;
+                    if (popc(s.wx[i] ^ y) < d) {
+                        const uint32_t e = atomicAdd(&s.npairs, 1u);
+                        if (e < kGwPairCap) s.u.pairs[e] = (k << 16) | i;
+                    }
+                }
+                if (rows > r0) my_tests += rows - r0;
+            }
+            __syncthreads();
+            // publish: the kills, and the pairs whose later entry survived
+            for (uint32_t r = tid; r < rows; r += kBlock) a.killbuf[lb + r * G] = s.flags[r];
+            const uint32_t np = s.npairs;
+            uint32_t kept = 0;
+            if (np <= kGwPairCap) {
+                uint32_t* pb = a.pairbuf + (size_t)lb * kGwPairCap;
+                for (uint32_t t0 = 0; t0 < np; t0 += kBlock) {
+                    const uint32_t e = t0 + tid;
+                    const uint32_t pr = e < np ? s.u.pairs[e] : 0u;
+                    const bool keep = e < np && s.flags[((pr & 0xffffu) - lb) / G] == 0;
+                    // block_append would reorder nothing here either; the
+                    // pairs' order does not matter, their count does
+                    const unsigned bal = __ballot_sync(kFull, keep);
+                    if (lane == 0) s.bs.warp_sum[warp_id()] = __popc(bal);
+                    __syncthreads();
+                    if (warp_id() == 0) {
+                        const uint32_t wv = lane < kWarps ? s.bs.warp_sum[lane] : 0u;
+                        uint32_t incl = wv;
+#pragma unroll
+                        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                            const uint32_t tv = __shfl_up_sync(kFull, incl, o2);
+                            if (lane >= o2) incl += tv;
+                        }
+                        if (lane < kWarps) s.bs.warp_sum[lane] = incl - wv;
+                        if (lane == 31) s.bs.warp_sum[kWarps] = incl;
+                    }
+                    __syncthreads();
+                    if (keep)
+                        pb[kept + s.bs.warp_sum[warp_id()] + __popc(bal & ((1u << lane) - 1u))] = pr;
+                    kept += s.bs.warp_sum[kWarps];
+                    __syncthreads();
+                }
+            }
+            if (tid == 0) a.pslot[(size_t)p * G + lb] = np <= kGwPairCap ? kept : kGwPairCap + 1u;
+        }
+        mark_phase(6);
+        ok = gw_sync(s, a, epoch);
+        if (!ok) break;
+        mark_phase(4);
+
+        // ---- every CTA decides the window from the same data
+        const uint32_t v = (uint32_t)tid < G ? ld_cg(a.pslot + (size_t)p * G + tid) : 0u;
+        {
+            // four entries per thread: one 4-byte load of their kill bytes
+            const uint32_t e0 = 4u * tid;
+            uint32_t kw = 0;
+            if (e0 + 4 <= Suse) {
+                kw = __ldcg(reinterpret_cast<const unsigned*>(a.killbuf + e0));
+            } else {
+                for (uint32_t k = 0; e0 + k < Suse; ++k)
+                    kw |= (uint32_t)__ldcg(a.killbuf + e0 + k) << (8 * k);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k)
+                if (e0 + k < Suse) s.state[e0 + k] = ((kw >> (8 * k)) & 0xffu) ? 2 : 0;
+        }
+        uint32_t P = 0;
+        {
+            const uint32_t ex = block_exclusive_scan(s.bs, min(v, kGwPairCap), &P);
+            if ((uint32_t)tid < G) s.pref[tid] = ex;
+        }
+        const bool over =
+            __syncthreads_or((uint32_t)tid < G && v > kGwPairCap) || P > kGwPairSmem;
+        uint32_t nacc = 0;
+        if (!over && P == 0u) {
+            // no conflict inside the window: the entries no previous accept
+            // rejected are the accepts
+            const uint32_t e0 = 4u * tid;
+            uint32_t keepm = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k)
+                if (e0 + k < Suse && s.state[e0 + k] == 0) keepm |= 1u << k;
+            uint32_t pos = block_exclusive_scan(s.bs, __popc(keepm), &nacc);
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k)
+                if ((keepm >> k) & 1u) {
+                    s.ax[pos] = s.wx[e0 + k];
+                    s.ax_off[pos] = (uint32_t)(R0 + s.woff[e0 + k]);
+                    ++pos;
+                }
+            __syncthreads();
+        } else if (!over) {
+            for (uint32_t g = warp_id(); g < G; g += kWarps) {
+                const uint32_t p0 = s.pref[g];
+                const uint32_t c = min(ld_cg(a.pslot + (size_t)p * G + g), kGwPairCap);
+                const uint32_t* src = a.pairbuf + (size_t)g * kGwPairCap;
+                for (uint32_t q = lane; q < c; q += 32) s.u.pairs[p0 + q] = ld_cg(src + q);
+            }
+            __syncthreads();
+            nacc = gw_pair_rounds(s, Suse, P, R0, &rounds_total);
+            ++pair_windows;
+        } else {
+            // drop the entries a previous accept rejects, then the conflict
+            // matrices
+            __syncthreads();
+            const uint32_t m = block_compact(s.bs, s.wx, s.woff, s.state, Suse);
+            uint64_t rt = 0;
+            nacc = block_resolve<false>(s.bs, s.wx, s.woff, s.flags, m, d, s.acc, s.acc_off,
+                                        s.u.M, rt, nullptr, 384u);
+            if (lb == 0) my_tests += rt;
+            for (uint32_t i = tid; i < nacc; i += kBlock) {
+                s.ax[i] = s.acc[i];
+                s.ax_off[i] = (uint32_t)(R0 + s.acc_off[i]);
+            }
+            __syncthreads();
+            ++fallbacks;
+        }
+        mark_phase(8);
+        Kprev = K;
+        K += nacc;
+        nprev = nacc;
+        ++windows;
+        surv_total += Suse;
+        // the next window aims at `target` survivors at the density this one
+        // had (at most twice as long)
+        {
+            const uint64_t used = Rnext - R0;
+            const uint64_t grow = 2ull * (uint64_t)W;
+            uint64_t want = Suse ? used * (uint64_t)a.target / Suse : grow;
+            if (want > grow) want = grow;
+            if (want < (uint64_t)a.wmin) want = a.wmin;
+            if (want > (uint64_t)a.wmax) want = a.wmax;
+            W = (uint32_t)want;
+        }
+        R0 = Rnext;
+    }
+    // the last window's accepts go to the output
+    if (ok) {
+        emit_prev();
+        mark_phase(7);
+    }
+    // statistics: warp-reduce, one atomic per warp
+    uint64_t tt = my_tests, m = my_marks, dn = dense;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        tt += __shfl_down_sync(kFull, tt, off);
+        m += __shfl_down_sync(kFull, m, off);
+        dn += __shfl_down_sync(kFull, dn, off);
+    }
+    if (lane == 0) {
+        if (tt) atomicAdd((unsigned long long*)&a.stats->executed_tests, (unsigned long long)tt);
+        if (m) atomicAdd((unsigned long long*)&a.stats->marks, (unsigned long long)m);
+        if (dn) atomicAdd((unsigned long long*)&a.stats->dense_tests, (unsigned long long)dn);
+    }
+    if (tid == 0 && lb == 0) {
+        gc_stats* st = a.stats;
+        st->codewords = K;
+        st->candidates = o.N;
+        st->windows = windows;
+        st->survivors = surv_total;
+        st->strategy = GC_STRATEGY_BITMAP_GRID;
+        st->pair_windows = pair_windows;
+        st->pair_fallbacks = fallbacks;
+        if (!ok || ld_acquire_gpu(a.ctrl + 1) != 0u) atomicMax((int*)&st->status, (int)GC_ERR_TIMEOUT);
+    }
+    if (timing) {
+        s.phase[11] = rounds_total;
+        for (int k = 0; k < 12; ++k) a.stats->phase_cycles[k] = s.phase[k];
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static size_t gw_align(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool grid_sweep_layout(const HostProblem& p, const gc_plan_t& plan, GridLayout* L,
+                       std::string* why) {
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+        *why = "cannot query the CUDA device";
+        return false;
+    }
+    if (p.n > kMaxN || p.orth) {
+        *why = "the grid bitmap sweep takes n <= 32 and no orthogonality constraint";
+        return false;
+    }
+    if ((size_t)optin < sizeof(GwSmem)) {
+        *why = "not enough shared memory per block for the grid bitmap sweep";
+        return false;
+    }
+    if (high_ball_len(p.n, p.d) >= (1u << 24)) {
+        *why = "ball table too large for the bitmap strategy";
+        return false;
+    }
+    int grid = sms;
+    if (plan.grid > 0) grid = std::min(grid, plan.grid);
+    grid = std::max(1, std::min(grid, kGwMaxCtas));
+    L->grid = grid;
+    L->smem_bytes = sizeof(GwSmem);
+    const size_t G = (size_t)grid;
+    size_t off = 0;
+    L->off_ctrl = off;    off += gw_align(256);
+    L->off_slot = off;    off += gw_align(sizeof(uint32_t) * 2 * G);
+    L->off_pslot = off;   off += gw_align(sizeof(uint32_t) * 2 * G);
+    L->off_segx = off;    off += gw_align(sizeof(uint32_t) * 2 * G * kGwChunk);
+    L->off_segoff = off;  off += gw_align(sizeof(uint32_t) * 2 * G * kGwChunk);
+    L->off_pairs = off;   off += gw_align(sizeof(uint32_t) * G * kGwPairCap);
+    L->off_kill = off;    off += gw_align(kGwSurvCap);
+    L->off_hball = off;   off += gw_align(4 * high_ball_len(p.n, p.d));
+    L->off_bitmap = off;  off += gw_align(((1ull << p.n) + 31) / 32 * 4);
+    L->total = off;
+    const uint64_t wcap = (uint64_t)grid * kGwChunk;
+    L->wmax = (uint32_t)std::min<uint64_t>(plan.window_max ? plan.window_max : wcap, wcap);
+    L->wmin = std::max<uint32_t>(
+        1, std::min<uint32_t>(plan.window_min ? plan.window_min : 256, L->wmax));
+    L->target = plan.survivor_target ? plan.survivor_target
+                                     : default_target(GC_STRATEGY_BITMAP_GRID, p);
+    return true;
+}
+
+static bool gw_fault_wait() {
+    const char* f = std::getenv("GC_FAULT");
+    return f && std::strcmp(f, "wait") == 0;
+}
+
+static uint32_t gw_timing_cta() {
+    const char* e = std::getenv("GC_TIMING_CTA");
+    return e ? (uint32_t)std::atoi(e) : 0u;
+}
+
+int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out,
+                      uint64_t capacity, gc_stats* d_stats, void* workspace, cudaStream_t s,
+                      std::string* why) {
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    cudaError_t e;
+    auto cuda_fail = [&](const char* what) {
+        *why = std::string(what) + ": " + cudaGetErrorString(e);
+        return GC_ERR_CUDA;
+    };
+    if ((e = cudaMemsetAsync(ws + L.off_ctrl, 0, 256, s)) != cudaSuccess)
+        return cuda_fail("control words");
+    const uint32_t hl = (uint32_t)high_ball_len(p.n, p.d);
+    const int nh = p.n > 5 ? p.n - 5 : 0;
+    int rc = launch_high_ball(nh, p.d - 1, reinterpret_cast<uint32_t*>(ws + L.off_hball), hl, s);
+    if (rc) {
+        *why = "ball table";
+        return rc;
+    }
+    if ((e = cudaFuncSetAttribute(grid_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)L.smem_bytes)) != cudaSuccess)
+        return cuda_fail("shared memory attribute");
+    const bool fault = gw_fault_wait();
+    GwArgs a{};
+    a.ord = order_of(p, p.filter, false);
+    a.d = p.d;
+    a.out = d_out;
+    a.cap = capacity;
+    a.stats = d_stats;
+    a.hball = reinterpret_cast<const uint32_t*>(ws + L.off_hball);
+    a.hball_len = hl;
+    a.bitmap = reinterpret_cast<uint32_t*>(ws + L.off_bitmap);
+    a.seg_x = reinterpret_cast<uint32_t*>(ws + L.off_segx);
+    a.seg_off = reinterpret_cast<uint32_t*>(ws + L.off_segoff);
+    a.slot = reinterpret_cast<uint32_t*>(ws + L.off_slot);
+    a.pslot = reinterpret_cast<uint32_t*>(ws + L.off_pslot);
+    a.pairbuf = reinterpret_cast<uint32_t*>(ws + L.off_pairs);
+    a.killbuf = ws + L.off_kill;
+    a.ctrl = reinterpret_cast<unsigned*>(ws + L.off_ctrl);
+    a.wmin = L.wmin;
+    a.wmax = L.wmax;
+    a.target = L.target;
+    a.timeout_cycles = fault ? 400000000ll : 20000000000ll;  // ~0.2 s / ~10 s at 2 GHz
+    a.timing_cta = gw_timing_cta();
+    a.extra_arrivals = fault ? 1u : 0u;
+    a.reversed = p.ord == GC_ORDER_GREVLEX ? 1u : 0u;
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)grid_sweep_kernel, dim3(L.grid), dim3(kBlock),
+                                    args, L.smem_bytes, s);
+    if (e != cudaSuccess) return cuda_fail("grid sweep launch");
+    return GC_OK;
+}
+
+}  // namespace gc

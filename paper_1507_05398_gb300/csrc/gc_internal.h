@@ -38,7 +38,12 @@ constexpr uint32_t kTargetBitmap = 1024;
 constexpr uint64_t kLargeSweep = 1ull << 28;
 // GC_TARGET_BITMAP overrides the bitmap target of sweeps below kLargeSweep
 // candidates (measurements).
+// The grid bitmap sweep decides at most 4096 survivors per window and cuts
+// the window after them; it aims a little above that, so that windows end at
+// the cut and little of the generated window is thrown away.
+constexpr uint32_t kTargetGrid = 4400;
 inline uint32_t default_target(int strategy, const HostProblem& p) {
+    if (strategy == GC_STRATEGY_BITMAP_GRID) return kTargetGrid;
     if (strategy != GC_STRATEGY_BITMAP) return kTargetDistance;
     if (p.valid < kLargeSweep) {
         const char* e = std::getenv("GC_TARGET_BITMAP");
@@ -152,6 +157,27 @@ int upload_batch(const BatchJob* jobs, int njobs, const BatchLayout& L, void* wo
                  cudaStream_t stream, std::string* why);
 int launch_batch_kernel(const BatchLayout& L, void* workspace, cudaStream_t stream,
                         std::string* why);
+
+// The grid bitmap sweep (gc_gridsweep.cu): one code on every SM, lockstep
+// windows.  Workspace offsets and launch shape.
+struct GridLayout {
+    int grid = 0;
+    size_t smem_bytes = 0;
+    size_t off_ctrl = 0, off_slot = 0, off_pslot = 0, off_segx = 0, off_segoff = 0;
+    size_t off_pairs = 0, off_kill = 0, off_hball = 0, off_bitmap = 0;
+    size_t total = 0;
+    uint32_t wmin = 0, wmax = 0, target = 0;
+};
+bool grid_sweep_layout(const HostProblem& p, const gc_plan_t& plan, GridLayout* L,
+                       std::string* why);
+// Ball table, control words and the cooperative launch, all on stream s.
+int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out,
+                      uint64_t capacity, gc_stats* d_stats, void* workspace, cudaStream_t s,
+                      std::string* why);
+// A batch or a server runs a grid-strategy job with the pipelined bitmap.
+inline int batch_strategy(int strategy) {
+    return strategy == GC_STRATEGY_BITMAP_GRID ? GC_STRATEGY_BITMAP : strategy;
+}
 
 // Step launchers (gc_steps.cu); each returns a GC_* code.
 int launch_unrank(const HostProblem& p, uint64_t rank0, uint64_t count, uint32_t* d_vec,

@@ -1709,6 +1709,8 @@ bool serve_describe(ServeLayout& L, const HostProblem& p, int strategy, uint32_t
                     uint64_t cap, gc_stats* d_stats, JobDesc* D, std::string* why) {
     gc_plan_t pl{};
     plan_for(p, &pl);
+    pl.strategy = batch_strategy(pl.strategy);
+    strategy = batch_strategy(strategy);
     if (strategy == GC_STRATEGY_DISTANCE || strategy == GC_STRATEGY_BITMAP) pl.strategy = strategy;
     const bool dist_fits = p.bound <= (uint64_t)L.cache_words + L.store_words;
     const bool bitmap_fits = (1ull << p.n) <= L.bitmap_bits && high_ball_len(p.n, p.d) < (1u << 24);

@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "LEX", "GRAY", "GRLEX", "GREVLEX", "BASIS", "NO_WEIGHT", "ORDERS",
     "CONSTRAINT_NONE", "CONSTRAINT_SELF_ORTHOGONAL",
-    "STRATEGY_AUTO", "STRATEGY_DISTANCE", "STRATEGY_BITMAP",
+    "STRATEGY_AUTO", "STRATEGY_DISTANCE", "STRATEGY_BITMAP", "STRATEGY_BITMAP_GRID",
     "GcError", "Problem", "Plan", "Stats", "lib", "library_path", "header_functions",
     "strerror", "candidate_count", "capacity_bound", "plan", "workspace_size",
     "generate", "generate_async", "generate_host",
@@ -33,7 +33,8 @@ __all__ = [
 LEX, GRAY, GRLEX, GREVLEX, BASIS = 0, 1, 2, 3, 4
 NO_WEIGHT = -1
 ORDERS = {"lex": LEX, "gray": GRAY, "grlex": GRLEX, "grevlex": GREVLEX, "basis": BASIS}
-STRATEGY_AUTO, STRATEGY_DISTANCE, STRATEGY_BITMAP = 0, 1, 2
+STRATEGY_AUTO, STRATEGY_DISTANCE, STRATEGY_BITMAP, STRATEGY_BITMAP_GRID = 0, 1, 2, 3
+_STRAT = {None: 0, "auto": 0, "distance": 1, "bitmap": 2, "grid": 3}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _HEADER = os.path.join(os.path.dirname(_HERE), "include", "gc.h")
@@ -243,7 +244,7 @@ def _plan_arg(strategy=None, **kw):
     if strategy is None and not kw:
         return None
     p = Plan()
-    p.strategy = {None: 0, "auto": 0, "distance": 1, "bitmap": 2}.get(strategy, strategy or 0)
+    p.strategy = _STRAT.get(strategy, strategy or 0)
     for k, v in kw.items():
         if v is not None:
             setattr(p, k, v)
@@ -288,7 +289,6 @@ def noalloc_scratch_bytes() -> int:
     return int(lib().gc_noalloc_scratch_bytes())
 
 
-_STRAT = {None: 0, "auto": 0, "distance": 1, "bitmap": 2}
 
 
 def _flat_layout(njobs, caps):

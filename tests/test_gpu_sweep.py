@@ -26,7 +26,7 @@ def gpu_code(n, d, o, w=-1, strategy=None, **kw):
     return code.cpu().numpy().view(np.uint32), st
 
 
-@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("strategy", ["distance", "bitmap", "grid"])
 @pytest.mark.parametrize("ordname", ORDERS)
 def test_exhaustive_small(strategy, ordname):
     """Every n <= 10, every d in [0, n+1], with and without a weight."""
@@ -68,7 +68,7 @@ def test_config_n20_d4(ordname):
     assert st.dense_tests == oracle.dense_tests(pos, 1 << 20)
 
 
-@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("strategy", ["distance", "bitmap", "grid"])
 @pytest.mark.parametrize("ordname", ORDERS)
 @pytest.mark.parametrize("n,d", [(16, 3), (17, 5), (18, 4), (19, 6), (21, 3)])
 def test_mid_sizes(strategy, ordname, n, d):
@@ -78,7 +78,7 @@ def test_mid_sizes(strategy, ordname, n, d):
     assert got.tolist() == want.tolist()
 
 
-@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("strategy", ["distance", "bitmap", "grid"])
 @pytest.mark.parametrize("ordname", ORDERS)
 @pytest.mark.parametrize("n,d,w", [(16, 4, 5), (18, 6, 6), (20, 4, 3), (14, 3, 7), (22, 6, 4)])
 def test_constant_weight(strategy, ordname, n, d, w):
@@ -88,7 +88,7 @@ def test_constant_weight(strategy, ordname, n, d, w):
     assert all(bin(int(x)).count("1") == w for x in got)
 
 
-@pytest.mark.parametrize("strategy", ["distance", "bitmap"])
+@pytest.mark.parametrize("strategy", ["distance", "bitmap", "grid"])
 def test_small_windows_and_degenerate(strategy):
     """Tiny windows force thousands of window steps; d = 2 keeps half the
     space (survivors beyond the resolver's capacity every window)."""
@@ -125,7 +125,7 @@ def test_large_configs_against_stored_oracle(row):
     """n = 31, d = 3 and n = 32, d = 4 (all orders), n = 28, d = 5 lex:
     compared with the oracle's stored list digest, plus closed forms."""
     n, d, o, w = row["n"], row["d"], row["ordering"], row["weight"]
-    strategies = ["bitmap", "distance"] if n == 28 else [None]
+    strategies = ["grid", "bitmap", "distance"] if n == 28 else [None, "bitmap"]
     for strategy in strategies:
         got, st = gpu_code(n, d, o, w, strategy)
         assert len(got) == row["size"]
@@ -133,6 +133,40 @@ def test_large_configs_against_stored_oracle(row):
         assert hashlib.sha256(got.astype("<u4").tobytes()).hexdigest() == row["sha256"]
     if (n, d, o) == (31, 3, "lex"):
         assert len(got) == 2 ** 26 and np.all(np.diff(got.astype(np.int64)) > 0)
+
+
+def test_large_bitmap_sweeps_plan_the_grid_strategy():
+    """A bitmap problem of 2^26 or more candidates is planned for the grid
+    strategy (every SM in every window); smaller ones keep the pipelined
+    bitmap sweep, which a batch or a server also runs for grid jobs."""
+    g = G()
+    assert g.plan(31, 3, "lex").strategy == g.STRATEGY_BITMAP_GRID
+    assert g.plan(32, 4, "grevlex").strategy == g.STRATEGY_BITMAP_GRID
+    assert g.plan(20, 4, "lex").strategy == g.STRATEGY_BITMAP
+    code, st = gpu_code(26, 3, "gray")
+    assert st.strategy == g.STRATEGY_BITMAP_GRID
+    assert code.tolist() == oracle.greedy_ball(26, 3, "gray").tolist()
+    res = g.generate_batch([(26, 3, "gray", -1, "grid"), (12, 3, "lex", -1)])
+    assert res[0][1].strategy == g.STRATEGY_BITMAP and res[0][0].tolist() == code.tolist()
+
+
+@pytest.mark.parametrize("o", ORDERS)
+@pytest.mark.parametrize("n,d,w", [(22, 3, -1), (23, 4, -1), (24, 5, -1), (22, 4, 9), (24, 3, 11)])
+def test_grid_strategy_mid_and_weighted(o, n, d, w):
+    """The grid strategy on codes of many windows, with and without a weight
+    (windows cut at 4096 survivors, pair lists, conflict-matrix fallbacks)."""
+    got, st = gpu_code(n, d, o, w, "grid")
+    want = oracle.greedy_ball(n, d, o, w)
+    assert got.tolist() == want.tolist()
+    assert st.strategy == G().STRATEGY_BITMAP_GRID and st.codewords == len(want)
+
+
+def test_grid_strategy_on_fewer_ctas():
+    """The grid strategy on a grid of 1, 2 and 7 CTAs (many rows per CTA)."""
+    want = oracle.greedy_ball(20, 4, "grlex")
+    for grid in (1, 2, 7):
+        got, _ = gpu_code(20, 4, "grlex", -1, "grid", grid=grid)
+        assert got.tolist() == want.tolist(), grid
 
 
 # (n, d, order, strategy, survivor target, whether pair lists must decide
