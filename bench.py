@@ -1,16 +1,25 @@
 """Benchmark of the ordered greedy code sweep on one GB300 (or N replicas).
 
-Workload (one "step"): the five codes n=24, d=8 lex (extended Golay) and
-n=20, d=4 in lex, Gray, graded-lex and graded-reverse-lex order, each one
-whole sweep over all 2^n candidates.  Metric: candidate-codeword distance
-tests per second, counted as dense-equivalent tests (for each candidate, the
-number of codewords accepted before it -- the tests a sweep without early
-exit performs, the paper's naive kernel) divided by the device time.
+Workload (one "step"): the nine large codes n=31, d=3 and n=32, d=4 in lex,
+Gray, graded-lex and graded-reverse-lex order (2^31 and 2^32 candidates, the
+exclusion-bitmap path with 256 / 512 MiB of bits) and n=28, d=5 lex, each
+one whole sweep over its candidates, one launch per code on the whole GPU,
+in the strategy the planner picks.  Metric: candidate-codeword distance tests
+per second, counted as dense-equivalent tests (for each candidate, the number
+of codewords accepted before it -- the tests a sweep without early exit
+performs, the paper's naive kernel) divided by the device time; the wall time
+per code is reported beside it, as the paper reports it (Section 6, Table 1).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs the same
 workload as an independent replica (the sweep of one code does not shard).
+Besides the headline, the line carries: the same codes through the C ABI's
+synchronous call into pinned host buffers (e2e), the five-code workload
+n=24 d=8 lex + n=20 d=4 in four orders as one batched launch, the 512
+seeded instances as one batch against one launch each, a short served
+replay, and CPU baselines (the oracle single-threaded on a bounded sample,
+and per instance on every host core over the 512 instances).
 """
 from __future__ import annotations
 
@@ -27,10 +36,19 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = [(24, 8, "lex"), (20, 4, "lex"), (20, 4, "gray"), (20, 4, "grlex"), (20, 4, "grevlex")]
-WORKLOAD_NAME = "n=24 d=8 lex + n=20 d=4 x {lex, gray, grlex, grevlex}"
+WORKLOAD = [(31, 3, "lex"), (31, 3, "gray"), (31, 3, "grlex"), (31, 3, "grevlex"),
+            (32, 4, "lex"), (32, 4, "gray"), (32, 4, "grlex"), (32, 4, "grevlex"),
+            (28, 5, "lex")]
+WORKLOAD_NAME = ("n=31 d=3 and n=32 d=4 in lex, gray, grlex and grevlex order + n=28 d=5 lex "
+                 "(9 whole sweeps, one launch each)")
+SMALL = [(24, 8, "lex"), (20, 4, "lex"), (20, 4, "gray"), (20, 4, "grlex"), (20, 4, "grevlex")]
+SMALL_NAME = "n=24 d=8 lex + n=20 d=4 x {lex, gray, grlex, grevlex}"
 METRIC = "candidate-codeword distance tests/s (dense-equivalent)"
+# bounded CPU sample of the workload: its one code the single-thread oracle
+# finishes in seconds (the n = 31 and 32 codes take minutes to an hour each)
+CPU_SAMPLE = (28, 5, "lex")
 L2_FLUSH_BYTES = 256 << 20
+HBM_FALLBACK_GBS = 6800.0
 
 
 def dist_env():
@@ -49,6 +67,11 @@ def cpu_model() -> str:
     except Exception:
         pass
     return platform.processor() or platform.machine()
+
+
+def name(code) -> str:
+    n, d, o = code[:3]
+    return f"n={n} d={d} {o}"
 
 
 class ClockSampler:
@@ -120,44 +143,82 @@ class ClockSampler:
                 mx = float(f[2])
             except ValueError:
                 continue
-            for name, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
-                    reasons.add(name)
+                    reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ CPU legs
+def oracle_sample():
+    """The single-thread exclusion-ball oracle on the workload's bounded
+    sample: (dense tests, seconds)."""
+    import oracle
+    oracle.build()
+    n, d, o = CPU_SAMPLE
+    t = time.perf_counter()
+    _, pos = oracle.greedy_ball(n, d, o, with_pos=True)
+    dt = time.perf_counter() - t
+    return oracle.dense_tests(pos, 1 << n), dt
+
+
+def _one_instance(p):
+    import oracle
+    n, d, o, w = p
+    t = time.perf_counter()
+    code = oracle.greedy_ball(n, d, o, w)
+    return len(code), time.perf_counter() - t
+
+
+def cpu_parallel_baseline():
+    """The 512 seeded batch instances, each through the exclusion-ball oracle,
+    spread over every host core (a spawned process pool)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import oracle
+    from paper_1507_05398_gb300.workloads import batch_instances
+    oracle.build()
+    probs = batch_instances()
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    with ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_one_instance, probs, chunksize=1))
+    wall = time.perf_counter() - t
+    return {"value": len(probs) / wall, "unit": "codes/s", "cores": cores, "kind": "oracle",
+            "sample": f"the {len(probs)} seeded batch instances (exclusion-ball oracle, one "
+                      f"process per core, {wall:.1f} s wall, "
+                      f"{sum(r[1] for r in res):.1f} s of CPU)",
+            "cpu": cpu_model()}
+
+
 # ------------------------------------------------------------------ reference
 def run_reference(args):
-    """The CPU oracle, single-threaded, as it stands: each step is one code of
-    the workload (rotating), so K steps cover a bounded sample of it."""
+    """The CPU oracle, single-threaded, as it stands, on the bounded sample of
+    the workload (one step = one whole n=28 d=5 lex sweep)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
     dense = 0
     seconds = 0.0
-    sample = []
     for i in range(args.warmup + args.steps):
-        n, d, o = WORKLOAD[i % len(WORKLOAD)]
-        t = time.perf_counter()
-        C, pos = oracle.greedy_pairwise(n, d, o, with_pos=True)
-        dt = time.perf_counter() - t
+        dn, dt = oracle_sample()
         if i >= args.warmup:
-            dense += oracle.dense_tests(pos, 1 << n)
+            dense += dn
             seconds += dt
-            sample.append(f"n={n} d={d} {o}")
     value = dense / seconds
+    sample = (f"{name(CPU_SAMPLE)}, exclusion-ball oracle, whole sweep per step "
+              f"({seconds / args.steps:.1f} s)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "tests/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * seconds / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (fully determined by n, d, order)",
-        "config": {"workload": WORKLOAD_NAME, "parallelism": "host, 1 thread"},
+        "config": {"workload": WORKLOAD_NAME, "parallelism": "host, 1 thread",
+                   "sample": name(CPU_SAMPLE)},
         "cpu_baseline": {"value": value, "unit": "tests/s", "cores": 1, "kind": "oracle",
-                         "sample": "; ".join(sample) + " (pairwise oracle, one code per step)",
-                         "cpu": cpu_model()},
+                         "sample": sample, "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "tests/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -165,21 +226,6 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
-def cpu_baseline_sample():
-    import oracle
-    oracle.build()
-    dense, secs, parts = 0, 0.0, []
-    for n, d, o in [(24, 8, "lex"), (20, 4, "lex")]:
-        t = time.perf_counter()
-        C, pos = oracle.greedy_pairwise(n, d, o, with_pos=True)
-        secs += time.perf_counter() - t
-        dense += oracle.dense_tests(pos, 1 << n)
-        parts.append(f"n={n} d={d} {o}")
-    return {"value": dense / secs, "unit": "tests/s", "cores": 1, "kind": "oracle",
-            "sample": " + ".join(parts) + " (pairwise oracle, whole sweeps, "
-                      f"{secs:.1f} s)", "cpu": cpu_model()}
-
-
 def _code_only(text: str) -> str:
     """C/C++ source with comments removed and whitespace runs collapsed
     (string and character literals kept as written)."""
@@ -205,14 +251,19 @@ def _code_only(text: str) -> str:
     return " ".join("".join(out).split())
 
 
-def kernel_source_hash() -> str:
-    """Hash of the CUDA/C++ sources' code (comments and layout ignored): the
-    recorded DRAM traffic stays valid across comment-only edits."""
+def kernel_source_hash(files=None) -> str:
+    """Hash of CUDA/C++ sources' code (comments and layout ignored): recorded
+    DRAM traffic stays valid across comment-only edits.  Default: every
+    source of the library."""
     import glob
     import hashlib
     csrc = os.path.join(ROOT, "paper_1507_05398_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
-                   + glob.glob(os.path.join(csrc, "*.h")))
+    if files is None:
+        files = sorted(glob.glob(os.path.join(csrc, "*.cu")) +
+                       glob.glob(os.path.join(csrc, "*.cuh")) +
+                       glob.glob(os.path.join(csrc, "*.h")))
+    else:
+        files = [os.path.join(csrc, f) for f in files]
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
@@ -220,19 +271,46 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the batched sweep from the committed ncu
-    summary, or None if the kernel sources changed since that capture."""
-    p = os.path.join(ROOT, "profiles", "sweep_kernel_bench_workload_traffic.md")
+GRID_SOURCES = ["gc_gridsweep.cu", "gc_block.cuh", "gc_device.cuh"]
+
+
+def recorded_traffic(profile: str, files=None):
+    """DRAM bytes per launch from a committed ncu summary, or None if the
+    kernel's sources changed since that capture."""
+    p = os.path.join(ROOT, "profiles", profile)
     try:
         txt = open(p).read()
     except OSError:
         return None
     vals = dict(l.split(":", 1) for l in txt.splitlines()
                 if l.startswith(("traffic_bytes_per_launch:", "kernel_source_sha256_16:")))
-    if vals.get("kernel_source_sha256_16", "").strip() != kernel_source_hash():
+    if vals.get("kernel_source_sha256_16", "").strip() != kernel_source_hash(files):
         return None
     return int(vals["traffic_bytes_per_launch"].strip())
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of the GB300s if
+    the measurement file is present, else the stated fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                v = d[k]
+                v = v.get("value", v) if isinstance(v, dict) else v
+                return float(v), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, TypeError):
+        pass
+    return HBM_FALLBACK_GBS, "fallback (no MEASURED_PEAKS.json in this run)"
+
+
+def algorithmic_bytes(n: int, codewords: int) -> int:
+    """The bitmap path's algorithmic bytes for one code: the 2^n-bit map
+    written once (zero fill) and read once (the lookups), every one of its
+    32-byte sectors marked at least once, and 4 bytes per codeword out."""
+    bitmap = (1 << n) // 8
+    return 3 * bitmap + 4 * codewords
 
 
 def run_ours(args):
@@ -254,173 +332,330 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    probs = [(n, d, o, -1) for n, d, o in WORKLOAD]
-    ngroups = len(probs) if args.groups is None else args.groups
-
-    # resident buffers: the whole workload as one prepared batch, one
-    # persistent launch per step, replayed from a CUDA graph
-    batch = G.BatchBuffers(probs, ngroups=ngroups)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    batch.launch(stream)
-    torch.cuda.synchronize()
-    try:
-        graph = batch.capture()
-        step = graph.replay
-        launch_kind = "CUDA graph replay of one batched persistent launch"
-    except Exception as e:  # capture refused: launch directly
-        print(f"bench: CUDA graph capture failed ({e}); launching directly", file=sys.stderr)
-        step = lambda: batch.launch(stream)  # noqa: E731
-        launch_kind = "one batched persistent launch"
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    results = batch.results()
-    for (code, st), p in zip(results, probs):
-        if st.status != 0:
-            raise RuntimeError(f"sweep failed for {p}: {st.as_dict()}")
-    dense = sum(st.dense_tests for _, st in results)
-    executed = sum(st.executed_tests for _, st in results)
-    launches_per_step = 1  # the sweep; ball tables were built when the batch was prepared
 
-    # timed region: K steps, L2 flushed before each, CUDA events per step
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    # resident buffers: output, statistics and workspace of every code
+    bufs = []
+    for n, d, o in WORKLOAD:
+        cap = G.capacity_bound(n, d, -1)
+        ws_bytes = G.workspace_size(n, d, o, -1)
+        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+        base = (-ws.data_ptr()) % 256
+        bufs.append((n, d, o, torch.empty(cap, dtype=torch.int32, device=dev),
+                     torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=dev),
+                     ws[base:base + ws_bytes]))
+
+    def one_step(events=None):
+        for k, (n, d, o, out, st, ws) in enumerate(bufs):
+            if events is not None:
+                events[k][0].record(stream)
+            G.generate_async(n, d, o, -1, out=out, stats=st, workspace=ws, stream=stream)
+            if events is not None:
+                events[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        one_step()
+    torch.cuda.synchronize()
+    stats = [G.stats_from(st) for *_, st, _ws in bufs]
+    for s, c in zip(stats, WORKLOAD):
+        if s.status != 0:
+            raise RuntimeError(f"sweep failed for {name(c)}: {s.as_dict()}")
+    dense = sum(s.dense_tests for s in stats)
+    executed = sum(s.executed_tests for s in stats)
+    marks = sum(s.marks for s in stats)
+    launches_per_step = 2 * len(WORKLOAD)  # the ball table and the sweep, per code
+
+    # timed region: K steps, L2 flushed before each, CUDA events per code
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in WORKLOAD] for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.fill_(s & 0xff)
-            ev[s][0].record(stream)
-            step()
-            ev[s][1].record(stream)
+            one_step(ev[s])
         torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    code_ms = [[a.elapsed_time(b) for a, b in step] for step in ev]
+    step_ms = [sum(x) for x in code_ms]
     mean_step_ms = statistics.mean(step_ms)
     if world > 1:
         t = torch.tensor([mean_step_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         mean_step_ms = float(t.item())
     value = world * dense / (mean_step_ms * 1e-3)
-    stats_now = [st for _, st in batch.results()]
+    per_code_ms = {name(c): statistics.mean(x[k] for x in code_ms)
+                   for k, c in enumerate(WORKLOAD)}
+    stats = [G.stats_from(st) for *_, st, _ws in bufs]
+    strategies = {1: "distance", 2: "bitmap", 3: "grid bitmap"}
+    clock_hz = 1e6 * (clk.summary()["sm_mhz"] or 2070.0)
 
-    # the same codes one launch each (gc_generate_async), for comparison
-    singles = []
-    for n, d, o, w in probs:
-        cap = G.capacity_bound(n, d, w)
-        ws_bytes = G.workspace_size(n, d, o, w)
-        ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
-        base = (-ws.data_ptr()) % 256
-        singles.append((n, d, o, w, torch.empty(cap, dtype=torch.int32, device=dev),
-                        torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=dev),
-                        ws[base:base + ws_bytes]))
-    per_code_ms = {}
-    for n, d, o, w, out, st, ws in singles:
-        G.generate_async(n, d, o, w, out=out, stats=st, workspace=ws, stream=stream)
-        times = []
-        for s in range(args.steps):
-            flush.fill_(s & 0xff)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            G.generate_async(n, d, o, w, out=out, stats=st, workspace=ws, stream=stream)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
-        per_code_ms[f"n={n} d={d} {o}"] = statistics.mean(times)
-    single_ms = sum(per_code_ms.values())
-
-    # end to end through the public API: generate_batch launches the batch
-    # (prepared on the first, untimed, call and kept), waits and copies the
-    # statistics and every output to the host in one transfer
-    e2e_times, d2h = [], G.batch_result_bytes(probs)
-    for s in range(0 if args.no_e2e else args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        res = G.generate_batch(probs, ngroups=ngroups)
-        if s >= args.warmup:
-            e2e_times.append(time.perf_counter() - t)
-        for (code, st), p in zip(res, probs):
-            if st.status != 0 or len(code) != st.codewords:
-                raise RuntimeError(f"end-to-end sweep failed for {p}: {st.as_dict()}")
+    # end to end through the C ABI's synchronous call: gc_generate into a
+    # pinned host buffer (its scratch allocation, the sweep, the copy of the
+    # code back to the host and the frees are all inside the timed call)
+    e2e_times, d2h = [], 0
+    e2e_steps = 0 if args.no_e2e else min(args.steps, 3)
+    if e2e_steps:
+        # pinned host buffers of each code's size (known from the runs above)
+        hosts = [torch.empty(max(s.codewords, 1), dtype=torch.int32, pin_memory=True)
+                 for s in stats]
+        L = G.lib()
+        for s in range(1 + e2e_steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            got = []
+            for (n, d, o), h in zip(WORKLOAD, hosts):
+                cnt = ctypes.c_uint64(h.numel())
+                rc = L.gc_generate(n, d, G.ORDERS[o], -1, ctypes.c_void_p(h.data_ptr()),
+                                   ctypes.byref(cnt))
+                if rc != 0:
+                    raise G.GcError(rc, "gc_generate")
+                got.append(int(cnt.value))
+            if s >= 1:
+                e2e_times.append(time.perf_counter() - t)
+        if got != [st.codewords for st in stats]:
+            raise RuntimeError("end-to-end code sizes differ from the device-resident run")
+        d2h = sum(4 * c + ctypes.sizeof(G.Stats) for c in got)
+        del hosts
     e2e_value = world * dense / statistics.mean(e2e_times) if e2e_times else None
 
-    # roofline of the sweep kernel: executed distance tests per second against
-    # the measured register-operand test rate of this GPU
-    peak, _ = G.probe_test_rate()
-    achieved = executed / (mean_step_ms * 1e-3)
+    # the bitmap roofline: algorithmic bytes per step over the event time
+    peak_gbs, peak_src = hbm_peak()
+    alg = sum(algorithmic_bytes(n, s.codewords) for (n, d, o), s in zip(WORKLOAD, stats))
+    achieved_gbs = alg / (mean_step_ms * 1e-3) / 1e9
+    mark_peak = G.probe_mark_rate()
+    test_peak, _ = G.probe_test_rate()
+    marks_per_s = marks / (mean_step_ms * 1e-3)
+    chain_us = {name(c): 1e3 * per_code_ms[name(c)] / max(s.windows, 1)
+                for c, s in zip(WORKLOAD, stats)}
+    traffic_launch = recorded_traffic("grid_sweep_n31d3_lex_dram.md", GRID_SOURCES)
+
+    extra = {}
+    if not args.only and not args.no_extras:
+        extra = extras(args, G, torch, stream, flush, test_peak)
+    del bufs
+    torch.cuda.empty_cache()
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    cpu = cpu_baseline_sample() if world == 1 and not args.no_cpu else None
-    clock_hz = 1e6 * (clk.summary()["sm_mhz"] or 2070.0)
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        dn, dt = oracle_sample()
+        cpu = {"value": dn / dt, "unit": "tests/s", "cores": 1, "kind": "oracle",
+               "sample": f"{name(CPU_SAMPLE)} (exclusion-ball oracle, one whole sweep, {dt:.1f} s)",
+               "cpu": cpu_model()}
     line = {
         "metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (fully determined by n, d, order)",
-        "config": {"workload": WORKLOAD_NAME, "codes_per_step": len(probs),
-                   "launch": f"{launch_kind}, {ngroups} SM groups",
-                   "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write)",
+        "config": {"workload": WORKLOAD_NAME, "codes_per_step": len(WORKLOAD),
+                   "launch": "one cooperative launch per code on the whole GPU (gc_generate_async)",
+                   "l2": f"inputs larger than L2 (256 / 512 MiB bitmaps) and flushed before each "
+                         f"step ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "strategies": {f"n={n} d={d} {o}": ("bitmap" if st.strategy == 2 else "distance")
-                                  for (n, d, o, w), st in zip(probs, stats_now)}},
-        "one_launch_per_code_ms": per_code_ms,
-        "one_launch_per_code_ms_per_step": single_ms,
-        "batched_speedup_vs_one_launch_per_code": single_ms / mean_step_ms,
+                   "strategies": {name(c): strategies.get(s.strategy, str(s.strategy))
+                                  for c, s in zip(WORKLOAD, stats)}},
+        "wall_ms_per_code": per_code_ms,
+        "codewords_per_code": {name(c): s.codewords for c, s in zip(WORKLOAD, stats)},
         "dense_tests_per_step": dense, "executed_tests_per_step": executed,
-        "windows_per_step": sum(st.windows for st in stats_now),
-        # the bitmap path's own measure: ball-mark word ORs (L2 atomics) per
-        # step and per second of the step; the n = 20 bitmaps are 128 KiB and
-        # stay in L2, so no HBM figure applies to them
-        "bitmap_marks_per_step": sum(st.marks for st in stats_now),
-        "bitmap_marks_per_s": sum(st.marks for st in stats_now) / (mean_step_ms * 1e-3),
-        "survivors_per_step": sum(st.survivors for st in stats_now),
-        "phase_ms_cta0": {f"n={n} d={d} {o}": dict(
-            {ph: (c if ph in ("rounds", "blocks") else round(1e3 * c / clock_hz, 4))
-             for ph, c in zip(G.Stats.PHASES, st.phase_cycles)},
-            windows=st.windows, survivors=st.survivors, pair_windows=st.pair_windows,
-            pair_fallbacks=st.pair_fallbacks)
-            for (n, d, o, w), st in zip(probs, stats_now)},
+        "executed_tests_per_s": executed / (mean_step_ms * 1e-3),
+        "bitmap_marks_per_step": marks, "bitmap_marks_per_s": marks_per_s,
+        "windows_per_code": {name(c): s.windows for c, s in zip(WORKLOAD, stats)},
+        "survivors_per_code": {name(c): s.survivors for c, s in zip(WORKLOAD, stats)},
         "e2e": {"value": e2e_value, "unit": "tests/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1e3 * statistics.mean(e2e_times) if e2e_times else None},
+                "ms_per_step": 1e3 * statistics.mean(e2e_times) if e2e_times else None,
+                "steps": len(e2e_times),
+                "call": "gc_generate(n, d, ordering, -1, pinned host buffer, &count) per code: "
+                        "scratch allocation, sweep, copy of the code to the host, frees; "
+                        "inputs are four integers per code (no host-to-device copy)"},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "tests/s",
-                     "frac": achieved / peak,
-                     "traffic": recorded_traffic() if not args.only else None,
-                     "kernel": "gc::sweep_kernel",
-                     "peak_source": "gc_probe_test_rate (register-operand XOR+popcount+compare, "
-                                    "measured in this run)"},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved_gbs / peak_gbs,
+                     "traffic": None if traffic_launch is None else traffic_launch,
+                     "kernel": "gc::grid_sweep_kernel",
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_step": alg},
+        "roofline_by_strategy": {
+            "bitmap_hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": peak_gbs,
+                           "frac": achieved_gbs / peak_gbs},
+            "bitmap_marks": {"achieved_ors_per_s": marks_per_s, "peak_ors_per_s": mark_peak,
+                             "frac": marks_per_s / mark_peak,
+                             "peak_source": "gc_probe_mark_rate (random word ORs in a 64 MiB "
+                                            "region, measured in this run)"},
+            "bitmap_window_chain_us": chain_us,
+            "distance": extra.get("distance_roofline"),
+        },
         "clocks": clk.summary(),
     }
+    for k, v in extra.items():
+        if k != "distance_roofline":
+            line[k] = v
     if cpu is not None:
         line["cpu_baseline"] = cpu
+        if not args.no_extras and not args.only:
+            line["cpu_parallel_baseline"] = cpu_parallel_baseline()
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def extras(args, G, torch, stream, flush, test_peak):
+    """The smaller workloads: the five-code batch (and its distance job alone
+    for the distance roofline), the 512 seeded instances batched against one
+    launch each, and a short served replay."""
+    out = {}
+    reps = max(3, min(args.steps, 20))
+    # five codes in one batched launch, replayed from a CUDA graph
+    probs = [(n, d, o, -1) for n, d, o in SMALL]
+    batch = G.BatchBuffers(probs, ngroups=len(probs))
+    batch.launch(stream)
+    torch.cuda.synchronize()
+    graph = batch.capture()
+    for _ in range(3):
+        graph.replay()
+    ts = []
+    for s in range(reps):
+        flush.fill_(s & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    res = batch.results()
+    small_ms = statistics.mean(ts)
+    one = {}
+    for (n, d, o, w) in probs:
+        cap = G.capacity_bound(n, d, w)
+        outb = torch.empty(cap, dtype=torch.int32, device=flush.device)
+        st = torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=flush.device)
+        wsz = G.workspace_size(n, d, o, w)
+        ws = torch.empty(wsz + 256, dtype=torch.uint8, device=flush.device)
+        base = (-ws.data_ptr()) % 256
+        wsa = ws[base:base + wsz]
+        G.generate_async(n, d, o, w, out=outb, stats=st, workspace=wsa, stream=stream)
+        tt = []
+        for s in range(reps):
+            flush.fill_(s & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.generate_async(n, d, o, w, out=outb, stats=st, workspace=wsa, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            tt.append(a.elapsed_time(b))
+        one[f"n={n} d={d} {o}"] = statistics.mean(tt)
+        if (n, d, o) == (24, 8, "lex"):
+            s = G.stats_from(st)
+            rate = s.executed_tests / (one[f"n={n} d={d} {o}"] * 1e-3)
+            out["distance_roofline"] = {
+                "code": "n=24 d=8 lex, alone on the whole GPU",
+                "achieved_tests_per_s": rate, "peak_tests_per_s": test_peak,
+                "frac": rate / test_peak,
+                "peak_source": "gc_probe_test_rate (register-operand XOR+popcount+compare, "
+                               "measured in this run)"}
+    out["workload_n24d8_n20d4"] = {
+        "workload": SMALL_NAME + " as one batched persistent launch (CUDA graph replay)",
+        "ms_per_step": small_ms,
+        "dense_tests_per_s": sum(st.dense_tests for _, st in res) / (small_ms * 1e-3),
+        "one_launch_per_code_ms": one,
+        "batched_speedup_vs_one_launch_per_code": sum(one.values()) / small_ms}
+    del batch, graph
+
+    # the 512 seeded instances: one batch against one launch each
+    from paper_1507_05398_gb300.workloads import batch_instances
+    inst = batch_instances()
+    b512 = G.BatchBuffers(inst)
+    b512.launch(stream)
+    torch.cuda.synchronize()
+    g512 = b512.capture()
+    g512.replay()
+    torch.cuda.synchronize()
+    tb = []
+    for s in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g512.replay()
+        b.record(stream)
+        b.synchronize()
+        tb.append(a.elapsed_time(b))
+    r512 = b512.results()
+    bad = [p for (c, st), p in zip(r512, inst) if st.status != 0]
+    if bad:
+        raise RuntimeError(f"batch instances failed: {bad[:3]}")
+    batch_ms = statistics.mean(tb)
+    # one launch each, on preallocated buffers (workspace of the largest)
+    caps = [G.capacity_bound(n, d, w) for n, d, o, w in inst]
+    outb = torch.empty(max(caps), dtype=torch.int32, device=flush.device)
+    st = torch.zeros(ctypes.sizeof(G.Stats), dtype=torch.uint8, device=flush.device)
+    wsz = max(G.workspace_size(n, d, o, w) for n, d, o, w in inst)
+    ws = torch.empty(wsz + 256, dtype=torch.uint8, device=flush.device)
+    base = (-ws.data_ptr()) % 256
+    wsa = ws[base:base + wsz]
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for (n, d, o, w), cap in zip(inst, caps):
+        G.generate_async(n, d, o, w, out=outb[:cap], stats=st, workspace=wsa, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    single_ms = a.elapsed_time(b)
+    out["batch512_ms"] = batch_ms
+    out["batch512_one_launch_each_ms"] = single_ms
+    out["batch512_vs_one_launch"] = single_ms / batch_ms
+    out["batch512_codes_per_s"] = len(inst) / (batch_ms * 1e-3)
+    out["batch512_workload"] = ("512 seeded instances (numpy PCG64 seed 1507): n~U{14..24}, "
+                                "d~U{3..8}, four orders, 25% constant weight w~U{3..n/2}; one "
+                                "persistent launch (CUDA graph replay) vs one launch per code")
+    del b512, g512, ws, outb
+    torch.cuda.synchronize()
+
+    # a short served replay (continuous batching)
+    from paper_1507_05398_gb300.serve import capacity, replay
+    from paper_1507_05398_gb300.workloads import serve_requests
+    nreq, load, seed = args.serve_requests, 0.8, 1507
+    with G.Server(max_n=28, pool_bytes=8 << 30, queue_capacity=2048) as srv:
+        probe = [p for _, p in serve_requests(512, seed + 1, 1.0)]
+        cap_jobs = capacity(srv, probe)
+        rate = load * cap_jobs
+        stream_req = serve_requests(nreq, seed, rate)
+        lat, makespan = replay(srv, stream_req)
+    lat_ms = sorted(1e3 * x for x in lat)
+    q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * len(lat_ms)))]  # noqa: E731
+    out["serve_p50_ms"] = q(0.50)
+    out["serve_p99_ms"] = q(0.99)
+    out["serve_jobs_per_s"] = nreq / makespan
+    out["serve_capacity_jobs_per_s"] = cap_jobs
+    out["serve_workload"] = (f"{nreq} seeded Poisson requests (seed {seed}) at {load} x the "
+                             f"measured capacity (lambda = {rate:.0f} jobs/s): 95% like the batch "
+                             "instances, 5% n~U{26..28} d~U{3,4}")
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 300, about 1 s; 5 for --impl reference)")
+                    help="timed steps (default: 3; 3 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=None,
-                    help="untimed warm-up steps (default: 10; 3 for --impl reference)")
+                    help="untimed warm-up steps (default: 3)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baselines")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API leg")
-    ap.add_argument("--groups", type=int, default=None,
-                    help="SM groups of the batched launch (default: one per code)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the smaller workloads (batch, 512 instances, serving)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the served replay (default 2000)")
     ap.add_argument("--only", default=None,
-                    help="run one code instead of the workload, e.g. '24,8,lex' (profiling)")
+                    help="run one code instead of the workload, e.g. '31,3,lex' (profiling)")
     args = ap.parse_args()
-    ref = args.impl == "reference"
     if args.steps is None:
-        args.steps = 5 if ref else 300
+        args.steps = 3
     if args.warmup is None:
-        args.warmup = 3 if ref else 10
+        args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
     else:

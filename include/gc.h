@@ -449,6 +449,14 @@ int gc_bitmap_scan(int n, int ordering, int weight_or_none,
  * reported SM clock (may be NULL). */
 int gc_probe_test_rate(double *tests_per_second, double *sm_clock_hz_hint);
 
+/* Measures, on the current device, how many bitmap word ORs per second the
+ * memory system sustains when every one goes to a pseudo-random word of a
+ * region of region_bytes (a power of two from 1 MiB to 1 GiB; 0 = 64 MiB,
+ * which stays in L2): the operation of the bitmap strategy's ball marking,
+ * so the ceiling of its marks.  Allocates and frees its region; runs two
+ * short kernels and synchronises.  GC_ERR_INVALID for a bad size. */
+int gc_probe_mark_rate(double *ors_per_second, size_t region_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,14 +6,12 @@
 // taking part in every step of every window.  Window t of W consecutive
 // ranks takes two phases, each ended by a grid-wide barrier (one arrival
 // counter, polled by one thread per CTA):
-//  A. every CTA ORs its share of the balls of window t-1's accepts into the
-//     exclusion bitmap and writes its share of them to the output, then
+//  A. every CTA writes its share of window t-1's accepts to the output, then
 //     generates its contiguous chunk of window t from the ranks (Section 4.2
-//     orders, closed form) and drops the candidates whose bit is set.  The
-//     bitmap then holds the radius-(d-1) balls of every codeword accepted in
-//     windows t-2 and earlier (marked before the last barrier) and whatever
-//     of window t-1's has landed.  The survivors go to the CTA's segment, in
-//     rank order.
+//     orders, closed form) and drops the candidates whose bit is set in the
+//     exclusion bitmap, which holds the radius-(d-1) balls of every codeword
+//     accepted in windows t-2 and earlier.  The survivors go to the CTA's
+//     segment, in rank order.
 //  B. every CTA gathers the window's survivors (the first kGwSurvCap; the
 //     window is cut after them) and tests its rows (entries i = CTA index
 //     mod grid) against window t-1's accepts, which every CTA holds in
@@ -22,6 +20,9 @@
 //     < d) of the entries no accept rejected.  A thread takes columns (one
 //     accept or one entry) and tests them against all the CTA's rows, so
 //     every warp has the same work and each loaded word serves every row.
+//     Between the columns it ORs its share of the balls of window t-1's
+//     accepts into the bitmap, complete when the phase's barrier passes, in
+//     time for window t+1.
 // Then every CTA, from the same data, decides the window exactly as the
 // serial loop would: with no pair, the entries no accept rejected are the
 // accepts; otherwise rounds over the pair list (an entry is rejected once an
@@ -251,20 +252,35 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
     // (a Hamming ball reversed is the ball around the reversed centre, and
     // weights do not change).  Only vectors after the codeword in the order
     // can still be candidates: lex and Gray skip the words wholly before it,
-    // the graded orders mask the lighter vectors.
+    // the graded orders mask the lighter vectors.  The ORs go out a few at a
+    // time (mark_some) between the row tests, which keep the popcount pipe
+    // busy while the atomics travel to L2.
     uint64_t my_marks = 0;
-    auto mark_share = [&](uint32_t nacc) {
+    uint64_t mq = 0, mq1 = 0;   // this thread's next pair and the share's end
+    uint32_t mi = 0, mj = 0, mnacc = 0, mdi = 0, mdj = 0;
+    auto mark_begin = [&](uint32_t nacc) {
         const uint32_t hl = a.hball_len;
+        mnacc = nacc;
+        mq = mq1 = 0;
         if (nacc == 0 || hl == 0) return;
         const uint64_t total = (uint64_t)nacc * hl;
         const uint64_t per = (total + G - 1) / G;
-        const uint64_t q0 = min((uint64_t)lb * per, total), q1 = min(q0 + per, total);
-        const uint64_t qs = q0 + tid;
-        uint32_t j = (uint32_t)(qs / nacc), i = (uint32_t)(qs - (uint64_t)j * nacc);
-        const uint32_t dj = kBlock / nacc, di = kBlock - dj * nacc;
-        for (uint64_t q = qs; q < q1; q += kBlock) {
-            const uint32_t c = a.reversed ? reverse_n(s.ax[i], n) : s.ax[i];
-            const uint32_t e = __ldg(a.hball + j);
+        const uint64_t q0 = min((uint64_t)lb * per, total);
+        mq1 = min(q0 + per, total);
+        mq = q0 + tid;
+        mj = (uint32_t)(mq / nacc);
+        mi = (uint32_t)(mq - (uint64_t)mj * nacc);
+        mdj = kBlock / nacc;
+        mdi = kBlock - mdj * nacc;
+    };
+    // this thread's ORs left
+    auto mark_left = [&]() -> uint32_t {
+        return mq < mq1 ? (uint32_t)((mq1 - mq + kBlock - 1) / kBlock) : 0u;
+    };
+    auto mark_some = [&](uint32_t count) {
+        for (uint32_t k = 0; k < count && mq < mq1; ++k) {
+            const uint32_t c = a.reversed ? reverse_n(s.ax[mi], n) : s.ax[mi];
+            const uint32_t e = __ldg(a.hball + mj);
             const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
             uint32_t mask = s.lowball[e & 7u][c & 31u];
             bool skip = false;
@@ -281,11 +297,12 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 atomicOr(a.bitmap + word, mask);
                 ++my_marks;
             }
-            i += di;
-            j += dj;
-            if (i >= nacc) {
-                i -= nacc;
-                ++j;
+            mq += kBlock;
+            mi += mdi;
+            mj += mdj;
+            if (mi >= mnacc) {
+                mi -= mnacc;
+                ++mj;
             }
         }
     };
@@ -310,11 +327,9 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
     for (; ok && R0 < o.N; ++t) {
         const int p = t & 1;
         const uint64_t span = min((uint64_t)W, o.N - R0);
-        // ---- A: the previous window's marks and output; this CTA's chunk,
-        // filtered by the bitmap
-        mark_share(nprev);
+        // ---- A: the previous window's output; this CTA's chunk, filtered by
+        // the bitmap (complete up to window t-2)
         emit_prev();
-        __syncthreads();
         mark_phase(0);
         {
             const uint64_t chunk = (span + G - 1) / G;
@@ -360,11 +375,16 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         if (tid == 0) {
             uint64_t rn = R0 + span;
             if (S > (uint32_t)kGwSurvCap) {
-                // the window ends after its kGwSurvCap-th survivor
-                uint32_t g = 0;
-                while (g + 1 < G && s.pref[g + 1] <= (uint32_t)kGwSurvCap - 1u) ++g;
-                rn = R0 + ld_cg(a.seg_off + ((size_t)p * G + g) * kGwChunk +
-                                ((uint32_t)kGwSurvCap - 1u - s.pref[g])) + 1;
+                // the window ends after its kGwSurvCap-th survivor, which
+                // sits in the segment of the last CTA g with pref[g] <= it
+                const uint32_t e = (uint32_t)kGwSurvCap - 1u;
+                uint32_t lo = 0, hi = G;
+                while (hi - lo > 1u) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s.pref[mid] <= e) lo = mid;
+                    else hi = mid;
+                }
+                rn = R0 + ld_cg(a.seg_off + ((size_t)p * G + lo) * kGwChunk + (e - s.pref[lo])) + 1;
             }
             s.bs.bcast64 = rn;
             s.npairs = 0;
@@ -405,8 +425,13 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         const uint64_t Rnext = s.bs.bcast64;
         mark_phase(5);
         {
+            // window t-1's marks, spread over the tests below: a slice after
+            // each column of them, the rest at the end
+            mark_begin(nprev);
+            const uint32_t mslice = (mark_left() + 7u) / 8u;
             // the previous window's accepts against every row
             for (uint32_t c = tid; c < nprev; c += kBlock) {
+                mark_some(mslice);
                 const uint32_t y = s.ax[c];
                 uint32_t r = 0;
                 for (; r + 4 <= rows; r += 4) {
@@ -421,8 +446,15 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                     if (popc(s.wx[lb + r * G] ^ y) < d) s.flags[r] = 1;
                 my_tests += rows;
             }
-            // the window's entries against the later rows: pairs (k, i)
-            for (uint32_t k = tid; k < Suse; k += kBlock) {
+            // the window's entries against the later rows: pairs (k, i).
+            // Entry k meets the rows after it, so a thread takes columns from
+            // both ends of each half of the window (tid, 2047 - tid, 2048 +
+            // tid, 4095 - tid) and every thread has about the same tests.
+#pragma unroll 1
+            for (uint32_t m = 0; m < (uint32_t)kGwSurvCap / kBlock; ++m) {
+                const uint32_t k = (m & 1u) ? kBlock * (m + 1u) - 1u - tid : kBlock * m + tid;
+                mark_some(mslice);
+                if (k >= Suse) continue;
                 const uint32_t y = s.wx[k];
                 const uint32_t r0 = k < lb ? 0u : (k - lb) / G + 1u;
                 for (uint32_t r = r0; r < rows; ++r) {
@@ -434,6 +466,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 }
                 if (rows > r0) my_tests += rows - r0;
             }
+            mark_some(mark_left());
             __syncthreads();
             // publish: the kills, and the pairs whose later entry survived
             for (uint32_t r = tid; r < rows; r += kBlock) a.killbuf[lb + r * G] = s.flags[r];

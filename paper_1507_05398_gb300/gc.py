@@ -24,7 +24,7 @@ __all__ = [
     "workspace_size64", "generate64", "generate64_async", "generate64_host",
     "product", "selforth_product",
     "unrank", "rank", "block_test", "resolve", "bitmap_mark", "bitmap_scan",
-    "probe_test_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
+    "probe_test_rate", "probe_mark_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
     "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
     "batch_result_bytes", "clear_batch_cache",
     "ServerConfig", "Server", "autotune", "set_tune_cache",
@@ -113,6 +113,7 @@ _SIGS = {
     "gc_bitmap_mark": (_i32, [_i32, _i32, _vp, _u64, _vp, _vp]),
     "gc_bitmap_scan": (_i32, [_i32, _i32, _i32, _vp, _u64, _u64, _vp, _u64, _vp, _vp]),
     "gc_probe_test_rate": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "gc_probe_mark_rate": (_i32, [ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "gc_generate_noalloc": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan), _vp, _u64, _vp,
                                    _vp]),
     "gc_batch_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Job), _i32, _i32]),
@@ -631,6 +632,13 @@ def bitmap_scan(n, ordering, weight, bitmap, rank0, count, capacity=None, stream
                                 _ptr(found), _stream(stream)), "gc_bitmap_scan")
     f = int(found.item())
     return out[:min(f, cap)], f
+
+
+def probe_mark_rate(region_bytes: int = 0) -> float:
+    """Bitmap word ORs per second at random words of a region (default 64 MiB)."""
+    r = ctypes.c_double(0)
+    _check(lib().gc_probe_mark_rate(ctypes.byref(r), region_bytes), "gc_probe_mark_rate")
+    return r.value
 
 
 def probe_test_rate() -> tuple[float, float]:
