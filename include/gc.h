@@ -350,15 +350,18 @@ int gc_server_destroy(gc_server *s);
 
 /* Allocation-free form of gc_generate_async (the paper has no counterpart;
  * this is a service for callers).  Some callers cannot call cudaMalloc when
- * they need a code: code running while a CUDA stream is being captured,
- * runtimes without a device allocator, or processes whose device memory is
- * owned by another framework's pool.  This entry point allocates nothing: the
- * caller passes only the output (d_out, capacity words) and d_stats, and the
- * sweep's scratch lives in one static device array of
- * gc_noalloc_scratch_bytes() bytes (32 MiB) inside the library, which every
- * GPU that loads the library holds until the process exits.
- *  - Problems whose scratch (gc_workspace_size) exceeds that size are rejected
- *    with GC_ERR_UNSUPPORTED and a message naming both sizes.
+ * they need a code: runtimes without a device allocator of their own,
+ * processes whose device memory is all handed to another framework's pool
+ * up front, or latency-critical paths that cannot take an allocation's
+ * synchronisation.  This entry point allocates nothing: the caller passes
+ * only the output (d_out, capacity words) and d_stats, and the sweep's
+ * scratch lives in one static device array of gc_noalloc_scratch_bytes()
+ * bytes (32 MiB) inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *  - Errors: GC_ERR_INVALID for a bad problem, plan or pointer;
+ *    GC_ERR_UNSUPPORTED for a valid problem whose scratch
+ *    (gc_workspace_size) exceeds that size -- the message names both sizes
+ *    -- or that the sweep's layout refuses (the message gives the reason).
  *  - The first call on a device looks up the array's device address (once
  *    per device, with that device current); make that first call before any
  *    stream capture.

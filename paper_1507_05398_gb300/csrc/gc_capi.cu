@@ -360,6 +360,27 @@ int gc_plan(const gc_problem* prob, gc_plan_t* out) {
     return GC_OK;
 }
 
+}  // extern "C"
+
+namespace gc {
+// The scratch bytes of one problem, with the reason when there are none:
+// GC_ERR_INVALID for a bad problem or plan, GC_ERR_UNSUPPORTED (and the
+// layout's reason) for a valid request the sweep's layout refuses.
+int workspace_bytes(const gc_problem* prob, const gc_plan_t* plan, size_t* out) {
+    *out = 0;
+    if (!prob) return fail(GC_ERR_INVALID, "null argument");
+    HostProblem p;
+    std::string why;
+    if (!make_problem(*prob, &p, &why)) return fail(GC_ERR_INVALID, why);
+    gc_plan_t pl;
+    if (!resolve_plan(p, plan, &pl)) return fail(GC_ERR_INVALID, "bad strategy");
+    *out = single_workspace(p, pl, &why);
+    return *out ? GC_OK : fail(GC_ERR_UNSUPPORTED, why);
+}
+}  // namespace gc
+
+extern "C" {
+
 size_t gc_workspace_size(const gc_problem* prob, const gc_plan_t* plan) {
     if (!prob) return 0;
     HostProblem p;

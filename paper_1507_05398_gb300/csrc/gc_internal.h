@@ -195,6 +195,11 @@ int launch_bitmap_scan(const HostProblem& p, const uint32_t* d_bitmap, uint64_t 
                        uint64_t count, uint32_t* d_out, uint64_t capacity, uint64_t* d_found,
                        uint64_t* d_counts, cudaStream_t s);
 
+// Scratch bytes of one problem (gc_workspace_size), or the error and its
+// reason: GC_ERR_INVALID (bad problem or plan), GC_ERR_UNSUPPORTED (valid,
+// but the sweep's layout refuses it).
+int workspace_bytes(const gc_problem* prob, const gc_plan_t* plan, size_t* out);
+
 // Records a message for gc_last_error() and returns code.
 int fail(int code, const std::string& msg);
 

@@ -2,13 +2,15 @@
 // allocation, for callers that cannot call cudaMalloc.
 //
 // Some callers cannot allocate device memory at the moment they need a code:
-// code running inside a CUDA stream capture where an allocation would break
-// the capture, allocator-free embedded runtimes, or hosts whose memory pool is
-// owned by another framework.  This entry point takes only the caller's
-// output and statistics buffers and keeps the sweep's scratch (grid barrier,
-// survivor segments, code store or exclusion bitmap, ball table) in one
-// file-scope device array of kNoAllocScratchBytes.  Every GPU that loads the
-// library holds that array until the process exits.
+// runtimes that have no device allocator of their own, hosts whose device
+// memory is all handed to another framework's pool up front (so a
+// cudaMalloc from this library would fail or fragment that pool), and code
+// on a latency-critical path where an allocation's synchronisation is not
+// acceptable.  This entry point takes only the caller's output and
+// statistics buffers and keeps the sweep's scratch (control words, survivor
+// segments, code store or exclusion bitmap, ball table) in one file-scope
+// device array of kNoAllocScratchBytes.  Every GPU that loads the library
+// holds that array until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -55,8 +57,9 @@ extern "C" size_t gc_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; 
 extern "C" int gc_generate_noalloc(const gc_problem* prob, const gc_plan_t* plan, uint32_t* d_out,
                                    uint64_t capacity, gc_stats* d_stats, void* stream) {
     if (!prob || !d_stats || (!d_out && capacity > 0)) return fail(GC_ERR_INVALID, "null argument");
-    const size_t need = gc_workspace_size(prob, plan);
-    if (need == 0) return fail(GC_ERR_INVALID, "invalid problem or plan");
+    size_t need = 0;
+    const int rc0 = workspace_bytes(prob, plan, &need);
+    if (rc0) return rc0;
     if (need > kNoAllocScratchBytes)
         return fail(GC_ERR_UNSUPPORTED,
                     "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch "

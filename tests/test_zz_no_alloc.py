@@ -1,13 +1,16 @@
 """gc_generate_noalloc, the allocation-free entry point for callers that
-cannot call cudaMalloc (stream capture, allocator-free runtimes, memory owned
-by another framework): through the C ABI its output must equal the regular
-gc_generate_async output, element for element, on two calls in a row (the
-static scratch is shared and keeps the previous call's contents).  Kept in a
-file of its own, collected last."""
+cannot call cudaMalloc (runtimes without a device allocator, device memory
+owned by another framework's pool, latency-critical paths): through the C ABI
+its output must equal the oracle's code and the regular gc_generate_async
+output, element for element, on two calls in a row (the static scratch is
+shared and keeps the previous call's contents).  Kept in a file of its own,
+collected last."""
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -23,6 +26,8 @@ def test_noalloc_matches_regular_entry_point_twice():
     assert G.noalloc_scratch_bytes() == 32 << 20
     for n, d, o, w, strategy in CASES:
         want = G.generate(n, d, o, w, strategy=strategy).cpu().numpy().view(np.uint32)
+        # the regular entry point agrees with the oracle (pins both paths)
+        assert want.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (n, d, o, w)
         cap = G.capacity_bound(n, d, w)
         for _ in range(2):
             out = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
@@ -44,3 +49,6 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     with pytest.raises(G.GcError) as e:  # a 2^30-bit exclusion map does not fit
         G.generate_noalloc(30, 3, "lex", out=out, stats=st, strategy="bitmap")
     assert e.value.code == 6 and "static scratch" in str(e.value)
+    with pytest.raises(G.GcError) as e:  # an invalid problem is GC_ERR_INVALID
+        G.generate_noalloc(33, 3, "lex", out=out, stats=st)
+    assert e.value.code == 1
