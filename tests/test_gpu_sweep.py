@@ -135,6 +135,19 @@ def test_large_configs_against_stored_oracle(row):
         assert len(got) == 2 ** 26 and np.all(np.diff(got.astype(np.int64)) > 0)
 
 
+def test_n32_d4_lex_is_the_parity_extension_of_n31_d3_lex():
+    """At full size, the GPU's n = 32, d = 4 lex code is its n = 31, d = 3 lex
+    code with an overall parity bit appended, word for word."""
+    a, _ = gpu_code(31, 3, "lex")
+    b, _ = gpu_code(32, 4, "lex")
+    par = a.copy()
+    for sh in (16, 8, 4, 2, 1):
+        par ^= par >> np.uint32(sh)
+    ext = (a.astype(np.uint64) << np.uint64(1)) | (par & np.uint32(1)).astype(np.uint64)
+    assert len(a) == len(b) == 2 ** 26
+    assert np.array_equal(ext, b.astype(np.uint64))
+
+
 def test_large_bitmap_sweeps_plan_the_grid_strategy():
     """A bitmap problem of 2^26 or more candidates is planned for the grid
     strategy (every SM in every window); smaller ones keep the pipelined

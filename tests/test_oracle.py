@@ -213,6 +213,44 @@ def test_parity_extension(n, d):
     assert ext == b.tolist()
 
 
+def _parity_ext(v: int) -> int:
+    return (v << 1) | (popc(v) & 1)
+
+
+def _large_rows():
+    import json
+    p = os.path.join(os.path.dirname(__file__), "golden", "large_expected.json")
+    return {(r["n"], r["d"], r["ordering"]): r for r in json.load(open(p))["codes"]}
+
+
+def test_parity_extension_relates_the_stored_n31_and_n32_codes():
+    """The stored n = 32, d = 4 lex code is the n = 31, d = 3 lex code with an
+    overall parity bit appended (the relation test_parity_extension checks
+    at n = 7, 11, 15): same size, and the stored first and last words map
+    onto each other."""
+    rows = _large_rows()
+    a, b = rows[(31, 3, "lex")], rows[(32, 4, "lex")]
+    assert a["size"] == b["size"] == 2 ** 26
+    assert [_parity_ext(x) for x in a["head"]] == b["head"]
+    assert _parity_ext(a["last"]) == b["last"]
+
+
+@pytest.mark.skipif(not os.environ.get("GC_SLOW"), reason="a minute of CPU; set GC_SLOW=1")
+def test_parity_extension_of_the_n31_oracle_code_gives_the_stored_n32_digest():
+    """The whole n = 31, d = 3 lex code from the oracle, extended by parity,
+    hashes to the stored n = 32, d = 4 lex digest (extended Hamming
+    [32,26,4]), which make_expected.py wrote from the n = 32 sweep."""
+    import hashlib
+    a = oracle.greedy_ball(31, 3, "lex").astype(np.uint32)
+    par = a.copy()
+    for sh in (16, 8, 4, 2, 1):
+        par ^= par >> np.uint32(sh)
+    ext = (a.astype(np.uint64) << np.uint64(1)) | (par & np.uint32(1)).astype(np.uint64)
+    assert ext.max() < 2 ** 32
+    digest = hashlib.sha256(ext.astype("<u4").tobytes()).hexdigest()
+    assert digest == _large_rows()[(32, 4, "lex")]["sha256"]
+
+
 # ---------------------------------------------------------------- edge cases
 @pytest.mark.parametrize("ordname", ORDERS)
 def test_degenerate_distances(ordname):
