@@ -91,7 +91,7 @@ typedef enum {
 
 /* Smallest rank space (log2) for which gc_plan() runs a bitmap problem with
  * GC_STRATEGY_BITMAP_GRID. */
-#define GC_GRID_MIN_LOG2 26
+#define GC_GRID_MIN_LOG2 24
 
 /* Extra constraints on the greedy. */
 enum {

@@ -22,6 +22,11 @@ def test_bounded_wait_expires_and_context_survives():
             G.generate(15, 3, "lex")
         assert e.value.code == 5  # GC_ERR_TIMEOUT
         assert time.time() - t < 30
+        # the grid sweep's barriers are bounded the same way
+        for strategy in ("grid", "bitmap"):
+            with pytest.raises(G.GcError) as e:
+                G.generate(16, 3, "gray", strategy=strategy)
+            assert e.value.code == 5, strategy
         # a batch: every job of the stuck group reports the timeout
         res = G.generate_batch([(12, 3, "lex", -1), (13, 4, "gray", -1)], ngroups=1)
         assert all(st.status == 5 for _, st in res)
