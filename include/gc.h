@@ -301,6 +301,23 @@ int gc_batch_create(const gc_job *jobs, int njobs, int ngroups, void *workspace,
 int gc_batch_launch(gc_batch *b, void *stream);
 int gc_batch_destroy(gc_batch *b);
 
+/* Measured per-instance plans for a batch (Section 6 observes that the best
+ * parallel form depends on how d compares with n; here it is measured per
+ * code, where it will run).  The jobs are laid out as gc_batch_create would
+ * lay them out with ngroups groups; then, for up to max_jobs (< 0: all)
+ * distinct problems, costliest first by the planner's cost model, every
+ * candidate plan -- distance or pipelined bitmap strategy (where each
+ * applies) x survivor target 256 / 512 / 1024 / 2048, which sets the window
+ * of B candidates per step -- runs once warm and once timed on as many CTAs
+ * as the batch gives the job, and the fastest is appended to the installed
+ * tuning cache with grid 0 (a cached grid would shrink a batch's launch).
+ * gc_batch_create, gc_batch_generate_async and gc_plan then use those plans.
+ * Reads only jobs[j].prob (the output and statistics pointers may be NULL).
+ * Needs a tuning cache (GC_ERR_INVALID otherwise); B-orderings are skipped
+ * (their basis is not part of the key).  Synchronous; allocates its own
+ * scratch.  *tuned receives how many problems were tuned. */
+int gc_batch_autotune(const gc_job *jobs, int njobs, int ngroups, int max_jobs, int *tuned);
+
 /* ---- serving: requests admitted while others run ------------------------ */
 
 /* Server settings (zero fields take the defaults in brackets). */

@@ -142,6 +142,9 @@ struct BatchLayout {
     size_t total = 0;
 };
 
+// Rough device cost of one job (used to balance and order batch jobs).
+double job_cost(const HostProblem& p, int strategy);
+
 // Splits the SMs into groups (ngroups <= 0: one per job, up to the SM count),
 // assigns jobs to groups (longest first) and lays out the workspace.
 bool batch_layout(const BatchJob* jobs, int njobs, int ngroups, BatchLayout* L, std::string* why);

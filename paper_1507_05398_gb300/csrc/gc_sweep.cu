@@ -1242,7 +1242,7 @@ static uint32_t resolve_block_size() {
 }
 
 // Rough device cost of one job, used to balance jobs over groups.
-static double job_cost(const HostProblem& p, int strategy) {
+double job_cost(const HostProblem& p, int strategy) {
     const double N = (double)p.valid;
     const double C = std::max(1.0, 0.5 * (double)p.bound);
     if (strategy == GC_STRATEGY_BITMAP) return N + 8.0 * C * (double)high_ball_len(p.n, p.d);

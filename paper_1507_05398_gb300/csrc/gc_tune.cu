@@ -9,6 +9,7 @@
 // itself use the cached plan for a problem it holds.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -105,6 +106,87 @@ bool tuned_plan(const HostProblem& p, gc_plan_t* out) {
     return found;
 }
 
+// Runs each candidate plan of a problem once to warm up and once timed, on
+// its own stream and scratch; returns the fastest (GC_ERR_UNSUPPORTED if
+// none ran).  A warm-up over twice the best so far is not timed again, and
+// one over four times it drops the rest of that strategy's candidates
+// (candidates come grouped by strategy, the planner's first).
+static int measure_plans(const gc_problem* prob, const HostProblem& p,
+                         const std::vector<gc_plan_t>& cands, gc_plan_t* best, double* best_ms) {
+    if (cands.empty()) return fail(GC_ERR_UNSUPPORTED, "no admissible plan");
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(GC_ERR_CUDA, "stream create");
+    uint32_t* d_out = nullptr;
+    gc_stats* d_stats = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_out, std::max<uint64_t>(p.bound, 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_stats, sizeof(gc_stats));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    double best_t = 1e300;
+    int rc = (e == cudaSuccess) ? GC_OK : fail(GC_ERR_OOM, cudaGetErrorString(e));
+    int dropped = GC_STRATEGY_AUTO;  // a strategy found hopeless
+    for (const gc_plan_t& c : cands) {
+        if (rc) break;
+        if (c.strategy == dropped) continue;
+        const size_t ws_bytes = gc_workspace_size(prob, &c);
+        if (ws_bytes == 0) continue;  // e.g. the bitmap would not fit
+        void* ws = nullptr;
+        if (cudaMalloc(&ws, ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {  // warm-up, then timed
+            cudaEventRecord(a, s);
+            ok = gc_generate_async(prob, &c, d_out, p.bound, d_stats, ws, ws_bytes, s) == GC_OK;
+            cudaEventRecord(b, s);
+            ok = ok && cudaEventSynchronize(b) == cudaSuccess;
+            // a warm-up over twice the best so far cannot win: not timed again
+            if (ok && rep == 0 && best_t < 1e300) {
+                cudaEventElapsedTime(&ms, a, b);
+                if (ms > 4.0 * best_t) dropped = c.strategy;
+                if (ms > 2.0 * best_t) break;
+            }
+        }
+        gc_stats st{};
+        ok = ok && cudaMemcpy(&st, d_stats, sizeof st, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             st.status == 0;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaFree(ws);
+        if (ok && ms < best_t) {
+            best_t = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (d_out) cudaFree(d_out);
+    if (d_stats) cudaFree(d_stats);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    if (best_t >= 1e300) return fail(GC_ERR_UNSUPPORTED, "no plan ran");
+    *best_ms = best_t;
+    return GC_OK;
+}
+
+// Candidate strategies of a problem: distance and the pipelined bitmap,
+// each where it applies, the planner's choice first.
+static std::vector<int> tune_strategies(const HostProblem& p) {
+    std::vector<int> out;
+    gc_plan_t base{};
+    plan_for(p, &base);
+    const bool dist_ok = p.bound < 0xffffffffull;
+    const bool bitmap_ok = !p.orth && high_ball_len(p.n, p.d) < (1u << 24);
+    const bool bitmap_first = batch_strategy(base.strategy) == GC_STRATEGY_BITMAP;
+    if (bitmap_first && bitmap_ok) out.push_back(GC_STRATEGY_BITMAP);
+    if (dist_ok) out.push_back(GC_STRATEGY_DISTANCE);
+    if (!bitmap_first && bitmap_ok) out.push_back(GC_STRATEGY_BITMAP);
+    return out;
+}
+
 }  // namespace gc
 
 using namespace gc;
@@ -130,13 +212,9 @@ int gc_autotune(const gc_problem* prob, gc_plan_t* best, double* best_ms) {
     std::vector<gc_plan_t> cands;
     gc_plan_t base{};
     plan_for(p, &base);
-    const int strategies[2] = {GC_STRATEGY_DISTANCE, GC_STRATEGY_BITMAP};
     const uint32_t targets[4] = {256, 512, 1024, 2048};
     const int grids[3] = {sms, std::max(1, sms / 4), std::max(1, sms / 8)};
-    for (int st : strategies) {
-        if (p.orth && st == GC_STRATEGY_BITMAP) continue;
-        if (st == GC_STRATEGY_BITMAP && high_ball_len(p.n, p.d) >= (1u << 24)) continue;
-        if (st == GC_STRATEGY_DISTANCE && p.bound >= 0xffffffffull) continue;
+    for (int st : tune_strategies(p))
         for (uint32_t t : targets)
             for (int g : grids) {
                 gc_plan_t c = base;
@@ -145,54 +223,9 @@ int gc_autotune(const gc_problem* prob, gc_plan_t* best, double* best_ms) {
                 c.grid = g;
                 cands.push_back(c);
             }
-    }
-    if (cands.empty()) return fail(GC_ERR_UNSUPPORTED, "no admissible plan");
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
-        return fail(GC_ERR_CUDA, "stream create");
-    uint32_t* d_out = nullptr;
-    gc_stats* d_stats = nullptr;
-    cudaError_t e = cudaMalloc((void**)&d_out, std::max<uint64_t>(p.bound, 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_stats, sizeof(gc_stats));
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    double best_t = 1e300;
-    int rc = (e == cudaSuccess) ? GC_OK : fail(GC_ERR_OOM, cudaGetErrorString(e));
-    for (const gc_plan_t& c : cands) {
-        if (rc) break;
-        const size_t ws_bytes = gc_workspace_size(prob, &c);
-        if (ws_bytes == 0) continue;  // e.g. the bitmap would not fit
-        void* ws = nullptr;
-        if (cudaMalloc(&ws, ws_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        float ms = 0.f;
-        bool ok = true;
-        for (int rep = 0; rep < 2 && ok; ++rep) {  // warm-up, then timed
-            cudaEventRecord(a, s);
-            ok = gc_generate_async(prob, &c, d_out, p.bound, d_stats, ws, ws_bytes, s) == GC_OK;
-            cudaEventRecord(b, s);
-            ok = ok && cudaEventSynchronize(b) == cudaSuccess;
-        }
-        gc_stats st{};
-        ok = ok && cudaMemcpy(&st, d_stats, sizeof st, cudaMemcpyDeviceToHost) == cudaSuccess &&
-             st.status == 0;
-        cudaEventElapsedTime(&ms, a, b);
-        cudaFree(ws);
-        if (ok && ms < best_t) {
-            best_t = ms;
-            *best = c;
-        }
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    if (d_out) cudaFree(d_out);
-    if (d_stats) cudaFree(d_stats);
-    cudaStreamDestroy(s);
+    double best_t = 0;
+    const int rc = measure_plans(prob, p, cands, best, &best_t);
     if (rc) return rc;
-    if (best_t >= 1e300) return fail(GC_ERR_UNSUPPORTED, "no plan ran");
     if (best_ms) *best_ms = best_t;
     std::string path;
     {
@@ -202,6 +235,80 @@ int gc_autotune(const gc_problem* prob, gc_plan_t* best, double* best_ms) {
     if (!path.empty() && cacheable(p)) {
         Entry en{p.n, p.d, p.ord, p.w, p.orth ? 1 : 0, device_name(), *best, best_t};
         if (!append_cache(path, en)) return fail(GC_ERR_INVALID, "cannot write the tuning cache");
+    }
+    return GC_OK;
+}
+
+int gc_batch_autotune(const gc_job* jobs, int njobs, int ngroups, int max_jobs, int* tuned) {
+    if (!jobs || njobs < 1 || !tuned) return fail(GC_ERR_INVALID, "null argument or no jobs");
+    *tuned = 0;
+    std::string path;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        path = cache_path_locked();
+    }
+    if (path.empty()) return fail(GC_ERR_INVALID, "gc_batch_autotune needs a tuning cache");
+    // the batch as gc_batch_create would plan and lay it out (cost model)
+    std::vector<BatchJob> B(njobs);
+    std::vector<gc_problem> probs(njobs);
+    for (int j = 0; j < njobs; ++j) {
+        std::string why;
+        if (!make_problem(jobs[j].prob, &B[j].p, &why))
+            return fail(GC_ERR_INVALID, "job " + std::to_string(j) + ": " + why);
+        plan_for(B[j].p, &B[j].plan);
+        B[j].plan.strategy = batch_strategy(B[j].plan.strategy);
+        B[j].plan.survivor_target = default_target(B[j].plan.strategy, B[j].p);
+        probs[j] = jobs[j].prob;
+    }
+    BatchLayout L;
+    std::string why;
+    if (!batch_layout(B.data(), njobs, ngroups, &L, &why)) return fail(GC_ERR_UNSUPPORTED, why);
+    // CTAs each job gets: its group's (with dynamic claiming, the smallest)
+    std::vector<int> ctas(njobs, L.ncta.empty() ? 1 : L.ncta[0]);
+    if (L.dynamic) {
+        const int m = *std::min_element(L.ncta.begin(), L.ncta.end());
+        std::fill(ctas.begin(), ctas.end(), m);
+    } else {
+        for (int g = 0; g < L.ngroups; ++g)
+            for (int q = L.job_begin[g]; q < L.job_end[g]; ++q) ctas[L.job_order[q]] = L.ncta[g];
+    }
+    // the costliest distinct problems first
+    std::vector<int> idx(njobs);
+    for (int j = 0; j < njobs; ++j) idx[j] = j;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return job_cost(B[x].p, B[x].plan.strategy) > job_cost(B[y].p, B[y].plan.strategy);
+    });
+    std::vector<int> done;
+    for (int j : idx) {
+        if (max_jobs >= 0 && *tuned >= max_jobs) break;
+        const HostProblem& p = B[j].p;
+        if (!cacheable(p)) continue;
+        bool seen = false;
+        for (int k : done)
+            seen = seen || (B[k].p.n == p.n && B[k].p.d == p.d && B[k].p.ord == p.ord &&
+                             B[k].p.w == p.w && B[k].p.orth == p.orth);
+        if (seen) continue;
+        done.push_back(j);
+        std::vector<gc_plan_t> cands;
+        const uint32_t targets[4] = {256, 512, 1024, 2048};
+        for (int st : tune_strategies(p))
+            for (uint32_t t : targets) {
+                gc_plan_t c = B[j].plan;
+                c.strategy = st;
+                c.survivor_target = t;
+                c.grid = ctas[j];
+                cands.push_back(c);
+            }
+        gc_plan_t best{};
+        double best_t = 0;
+        const int rc = measure_plans(&probs[j], p, cands, &best, &best_t);
+        if (rc) return rc;
+        // recorded for every launch size: a batch takes its grid from the
+        // SMs, and a cached grid would shrink the whole launch
+        best.grid = 0;
+        Entry en{p.n, p.d, p.ord, p.w, p.orth ? 1 : 0, device_name(), best, best_t};
+        if (!append_cache(path, en)) return fail(GC_ERR_INVALID, "cannot write the tuning cache");
+        ++*tuned;
     }
     return GC_OK;
 }

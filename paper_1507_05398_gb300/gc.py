@@ -27,7 +27,7 @@ __all__ = [
     "probe_test_rate", "probe_mark_rate", "stats_from", "generate_noalloc", "noalloc_scratch_bytes",
     "Job", "BatchBuffers", "batch_workspace_size", "batch_generate_async", "generate_batch",
     "batch_result_bytes", "clear_batch_cache",
-    "ServerConfig", "Server", "autotune", "set_tune_cache",
+    "ServerConfig", "Server", "autotune", "batch_autotune", "set_tune_cache",
 ]
 
 LEX, GRAY, GRLEX, GREVLEX, BASIS = 0, 1, 2, 3, 4
@@ -126,6 +126,7 @@ _SIGS = {
     "gc_autotune": (_i32, [ctypes.POINTER(Problem), ctypes.POINTER(Plan),
                            ctypes.POINTER(ctypes.c_double)]),
     "gc_set_tune_cache": (_i32, [ctypes.c_char_p]),
+    "gc_batch_autotune": (_i32, [ctypes.POINTER(Job), _i32, _i32, _i32, ctypes.POINTER(_i32)]),
     "gc_batch_generate_async": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp]),
     "gc_batch_create": (_i32, [ctypes.POINTER(Job), _i32, _i32, _vp, ctypes.c_size_t, _vp,
                                ctypes.POINTER(ctypes.c_void_p)]),
@@ -717,6 +718,22 @@ def autotune(n, d, ordering="lex", weight=NO_WEIGHT, constraint=None):
     _check(lib().gc_autotune(ctypes.byref(_problem(n, d, ordering, weight, constraint)),
                              ctypes.byref(best), ctypes.byref(ms)), "gc_autotune")
     return best, ms.value
+
+
+def batch_autotune(problems, ngroups=0, max_jobs=-1) -> int:
+    """gc_batch_autotune: measured plans for the costliest distinct problems
+    of a batch, on the CTAs the batch gives each, into the installed tuning
+    cache.  problems: (n, d, ordering, weight[, strategy[, constraint]]).
+    Returns how many problems were tuned."""
+    ps = [tuple(p) + (None,) * (6 - len(p)) for p in problems]
+    jobs = (Job * len(ps))()
+    for k, (n, d, o, w, st, c) in enumerate(ps):
+        jobs[k].prob = _problem(n, d, o, w, c)
+        jobs[k].strategy = _STRAT.get(st, st or 0)
+    tuned = _i32(0)
+    _check(lib().gc_batch_autotune(jobs, len(ps), ngroups, max_jobs, ctypes.byref(tuned)),
+           "gc_batch_autotune")
+    return int(tuned.value)
 
 
 def set_tune_cache(path):
