@@ -8,10 +8,16 @@
 // counter, polled by one thread per CTA):
 //  A. every CTA writes its share of window t-1's accepts to the output, then
 //     generates its contiguous chunk of window t from the ranks (Section 4.2
-//     orders, closed form) and drops the candidates whose bit is set in the
-//     exclusion bitmap, which holds the radius-(d-1) balls of every codeword
-//     accepted in windows t-2 and earlier.  The survivors go to the CTA's
-//     segment, in rank order.
+//     orders, closed form) and drops the candidates the exclusion bitmap
+//     covers.  The bitmap holds the balls of every codeword accepted in
+//     windows t-2 and earlier: for d <= 3 of radius d-1, and a candidate is
+//     covered when its own bit is set; for d >= 4 of radius d-2, and a
+//     candidate is covered when a vector within distance 1 of it is set (a
+//     vector within d-1 of a codeword is within 1 of one within d-2 of it).
+//     The radius-(d-2) ball is several times smaller (379 words against
+//     about 3300 at n = 32, d = 4), and most candidates are covered at the
+//     first of their probes.  The survivors go to the CTA's segment, in rank
+//     order.
 //  B. every CTA gathers the window's survivors (the first kGwSurvCap; the
 //     window is cut after them) and tests its rows (entries i = CTA index
 //     mod grid) against window t-1's accepts, which every CTA holds in
@@ -75,6 +81,7 @@ struct GwArgs {
     uint32_t timing_cta;
     uint32_t extra_arrivals;  // fault injection: barriers wait for this many CTAs more
     uint32_t reversed;        // 1: the bitmap is indexed by the bit-reversed vector
+    uint32_t probe;           // 1: radius-(d-2) balls marked, lookups probe radius 1
 };
 
 struct __align__(16) GwSmem {
@@ -284,7 +291,10 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             const uint32_t cw = c >> 5, word = cw ^ (e >> 3);
             uint32_t mask = s.lowball[e & 7u][c & 31u];
             bool skip = false;
-            if (o.ord == kLex) {
+            if (a.probe) {
+                // radius-(d-2) balls are witnesses for the probes, on either
+                // side of the frontier: the whole ball is marked
+            } else if (o.ord == kLex) {
                 skip = word < cw;
                 if (word == cw) mask &= ~((2u << (c & 31u)) - 1u);
             } else if (o.ord == kGray) {
@@ -344,7 +354,24 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                     keep = unrank(o, s.C, r, x);
                             if (keep) {
                         const uint32_t key = a.reversed ? reverse_n(x, n) : x;
-                        keep = !((ld_cg(a.bitmap + (key >> 5)) >> (key & 31u)) & 1u);
+                        const uint32_t w0 = key >> 5, b = key & 31u;
+                        if (!a.probe) {
+                            keep = !((ld_cg(a.bitmap + w0) >> b) & 1u);
+                        } else {
+                            // covered iff a marked vector is within distance 1:
+                            // in the word, or this bit of a word one high bit away
+                            bool hit = (ld_cg(a.bitmap + w0) & s.lowball[1][b]) != 0u;
+                            const int nh = n > 5 ? n - 5 : 0;
+                            for (int j0 = 0; j0 < nh && !hit; j0 += 8) {
+                                uint32_t v[8];
+#pragma unroll
+                                for (int u = 0; u < 8; ++u)
+                                    v[u] = j0 + u < nh ? ld_cg(a.bitmap + (w0 ^ (1u << (j0 + u)))) : 0u;
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) hit = hit || ((v[u] >> b) & 1u);
+                            }
+                            keep = !hit;
+                        }
                     }
                 }
                 na = block_append(s.bs, keep, x, (uint32_t)(r - R0), s.wx, s.woff, na);
@@ -701,9 +728,15 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     };
     if ((e = cudaMemsetAsync(ws + L.off_ctrl, 0, 256, s)) != cudaSuccess)
         return cuda_fail("control words");
-    const uint32_t hl = (uint32_t)high_ball_len(p.n, p.d);
+    // d >= 4: marks of radius d-2 and lookups that probe radius 1 (a
+    // candidate within d-1 of a codeword is within 1 of a vector within d-2
+    // of it); the ball to mark is several times smaller
+    uint32_t probe = p.d >= 4 ? 1u : 0u;
+    if (const char* e = std::getenv("GC_GRID_PROBE")) probe = std::atoi(e) != 0 && p.d >= 2 ? 1u : 0u;
+    const int rad = p.d - 1 - (int)probe;
+    const uint32_t hl = (uint32_t)high_ball_len(p.n, rad + 1);
     const int nh = p.n > 5 ? p.n - 5 : 0;
-    int rc = launch_high_ball(nh, p.d - 1, reinterpret_cast<uint32_t*>(ws + L.off_hball), hl, s);
+    int rc = launch_high_ball(nh, rad, reinterpret_cast<uint32_t*>(ws + L.off_hball), hl, s);
     if (rc) {
         *why = "ball table";
         return rc;
@@ -735,6 +768,7 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     a.timing_cta = gw_timing_cta();
     a.extra_arrivals = fault ? 1u : 0u;
     a.reversed = p.ord == GC_ORDER_GREVLEX ? 1u : 0u;
+    a.probe = probe;
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel((const void*)grid_sweep_kernel, dim3(L.grid), dim3(kBlock),
                                     args, L.smem_bytes, s);

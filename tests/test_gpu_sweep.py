@@ -174,6 +174,20 @@ def test_grid_strategy_mid_and_weighted(o, n, d, w):
     assert st.strategy == G().STRATEGY_BITMAP_GRID and st.codewords == len(want)
 
 
+@pytest.mark.parametrize("probe", ["0", "1"])
+def test_grid_radius_split_both_ways(probe, monkeypatch):
+    """The grid sweep either marks radius-(d-1) balls and looks up one bit,
+    or (the default for d >= 4) marks radius-(d-2) balls and probes the
+    candidate's radius-1 neighbourhood; GC_GRID_PROBE forces either.  Both
+    give the oracle's code, in every order, with and without a weight."""
+    monkeypatch.setenv("GC_GRID_PROBE", probe)
+    for n, d, o, w in [(18, 3, "lex", -1), (19, 4, "gray", -1), (20, 4, "grevlex", -1),
+                       (20, 5, "grlex", -1), (21, 6, "lex", -1), (18, 4, "grevlex", 7),
+                       (20, 4, "gray", 9), (9, 4, "lex", -1), (5, 3, "grlex", -1)]:
+        got, st = gpu_code(n, d, o, w, "grid")
+        assert got.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (probe, n, d, o, w)
+
+
 def test_grid_strategy_on_fewer_ctas():
     """The grid strategy on a grid of 1, 2 and 7 CTAs (many rows per CTA)."""
     want = oracle.greedy_ball(20, 4, "grlex")
