@@ -3,43 +3,43 @@
 //
 // It computes what the pipelined bitmap sweep of gc_sweep.cu computes -- the
 // ordered greedy code of Section 4 -- for one code at a time, with every SM
-// taking part in every step of every window.  Window t of W consecutive
-// ranks takes two phases, each ended by a grid-wide barrier (one arrival
-// counter, polled by one thread per CTA):
-//  A. every CTA writes its share of window t-1's accepts to the output, then
-//     generates its contiguous chunk of window t from the ranks (Section 4.2
-//     orders, closed form) and drops the candidates the exclusion bitmap
-//     covers.  The bitmap holds the balls of every codeword accepted in
-//     windows t-2 and earlier: for d <= 3 of radius d-1, and a candidate is
-//     covered when its own bit is set; for d >= 4 of radius d-2, and a
-//     candidate is covered when a vector within distance 1 of it is set (a
-//     vector within d-1 of a codeword is within 1 of one within d-2 of it).
-//     The radius-(d-2) ball is several times smaller (379 words against
-//     about 3300 at n = 32, d = 4), and most candidates are covered at the
-//     first of their probes.  The survivors go to the CTA's segment, in rank
-//     order.
+// taking part in every step of every window.  The exclusion bitmap holds the
+// radius-(d-2) balls of the codewords accepted so far, and a vector is
+// covered (within distance d-1 of one of them) iff a marked vector lies
+// within distance 1 of it: its own word, under the in-word radius-1 mask, or
+// its bit in the n - 5 words one high bit away.  The radius-(d-2) ball is
+// several times smaller than the radius-(d-1) one (32 against about 350
+// words per codeword at n = 31, d = 3; 379 against about 3300 at n = 32,
+// d = 4), and most covered candidates show it at the first probe.  Window t
+// of W consecutive ranks takes two phases, each ended by a grid-wide barrier
+// (one arrival counter, polled by one thread per CTA):
+//  A. every CTA writes its share of window t-1's accepts to the output, ORs
+//     its share of their balls into the bitmap, then generates its
+//     contiguous chunk of window t from the ranks (Section 4.2 orders,
+//     closed form) and drops the candidates the bitmap covers -- it is
+//     complete up to window t-2 and holds part of window t-1.  The survivors
+//     go to the CTA's segment, in rank order.
 //  B. every CTA gathers the window's survivors (the first kGwSurvCap; the
-//     window is cut after them) and tests its rows (entries i = CTA index
-//     mod grid) against window t-1's accepts, which every CTA holds in
-//     shared memory -- a hit rejects the entry -- and against every earlier
-//     entry of the window, listing the conflicting pairs (Hamming distance
-//     < d) of the entries no accept rejected.  A thread takes columns (one
-//     accept or one entry) and tests them against all the CTA's rows, so
-//     every warp has the same work and each loaded word serves every row.
-//     Between the columns it ORs its share of the balls of window t-1's
-//     accepts into the bitmap, complete when the phase's barrier passes, in
-//     time for window t+1.
+//     window is cut after them).  It probes its rows (entries i = CTA index
+//     mod grid) against the bitmap, now complete up to window t-1 -- a hit
+//     rejects the entry -- and tests them against every earlier entry of the
+//     window, listing the conflicting pairs (Hamming distance < d).  A
+//     thread takes columns (entries) and tests each against all the CTA's
+//     rows, which sit contiguous in shared memory, four to a 16-byte load.
 // Then every CTA, from the same data, decides the window exactly as the
 // serial loop would: with no pair, the entries no accept rejected are the
 // accepts; otherwise rounds over the pair list (an entry is rejected once an
 // earlier neighbour is accepted and accepted once every earlier neighbour is
 // rejected); when the list is too long, the conflict matrices of
 // block_resolve.  Every CTA keeps the accepts for the next window.
+// A second form (GC_GRID_EARLY=0) marks window t-1's balls between the row
+// tests of phase B and tests the rows against window t-1's accepts instead
+// of probing them; with GC_GRID_PROBE=0 as well, it marks radius-(d-1) balls
+// and a lookup reads one bit.
 // Compared with the pipelined form, no CTA waits on another's flag word
 // (the flag all-gathers of that design took several microseconds each at
 // 152 CTAs, the counter barrier about two), nothing runs on one SM while the
-// others wait, and the test against the previous window's accepts, the pair
-// search and the marks are spread over every SM.
+// others wait, and the pair search and the marks are spread over every SM.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +56,7 @@ constexpr int kGwChunk = 4096;          // candidates per CTA per window
 constexpr uint32_t kGwPairCap = 2048;   // pairs one CTA may list per window
 constexpr uint32_t kGwPairSmem = 16384; // pairs a CTA takes into shared memory
 constexpr int kGwMaxCtas = kBlock;      // one count per thread in the prefix scans
+constexpr int kGwProbeBatch = 14;       // high-bit probes a lookup issues at once
 static_assert(kGwSurvCap <= 65536, "pairs pack two entry indices in 16 bits each");
 static_assert(kGwSurvCap == 4 * kBlock, "the accept compaction gives a thread four entries");
 static_assert(kGwPairCap <= kGwPairSmem, "a CTA's own pairs are staged in the pair area");
@@ -82,6 +83,8 @@ struct GwArgs {
     uint32_t extra_arrivals;  // fault injection: barriers wait for this many CTAs more
     uint32_t reversed;        // 1: the bitmap is indexed by the bit-reversed vector
     uint32_t probe;           // 1: radius-(d-2) balls marked, lookups probe radius 1
+    uint32_t early;           // 1 (with probe): window t-1's balls marked in phase A of
+                              // window t, rows probed in phase B instead of tested
 };
 
 struct __align__(16) GwSmem {
@@ -93,7 +96,7 @@ struct __align__(16) GwSmem {
     __align__(16) uint32_t woff[kGwSurvCap];
     __align__(16) uint32_t ax[kGwSurvCap];      // the previous window's accepts
     __align__(16) uint32_t ax_off[kGwSurvCap];  // and their ranks (n <= 32)
-    __align__(16) uint32_t acc[kGwSurvCap];     // block_resolve's output
+    __align__(16) uint32_t acc[kGwSurvCap];     // block_resolve's output; B: own rows
     __align__(16) uint32_t acc_off[kGwSurvCap];
     uint8_t state[kGwSurvCap];                  // 0 undecided, 1 accepted, 2 rejected
     uint8_t flags[2 * kGwSurvCap];              // row kills (B); killed / blocked (rounds)
@@ -109,26 +112,28 @@ struct __align__(16) GwSmem {
 };
 
 // CTA-wide grid barrier: one arrival per CTA on a counter that only grows;
-// the barrier of epoch e is passed once it reaches (e + 1) * arrivals.
-// Bounded: on a timeout (or an error another CTA reported) returns false.
+// the barrier of epoch e is passed once it reaches (e + 1) * arrivals.  The
+// arrival is a release reduction after the CTA barrier and the wait an
+// acquire load before the next one, so the CTA's writes before the barrier
+// are visible to every CTA after it.  Bounded: on a timeout (or an error
+// another CTA reported) returns false.
 __device__ bool gw_sync(GwSmem& s, const GwArgs& a, uint32_t& epoch) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(a.ctrl, 1u);
+        red_add_release_gpu(a.ctrl, 1u);
         const unsigned target = (epoch + 1u) * (gridDim.x + a.extra_arrivals);
         const long long t0 = clock64();
         uint32_t fine = 1u;
-        for (;;) {
+        for (uint32_t it = 1;; ++it) {
             if ((int)(ld_acquire_gpu(a.ctrl) - target) >= 0) break;
-            if (ld_acquire_gpu(a.ctrl + 1) != 0u) { fine = 0u; break; }
+            if ((it & 15u) != 0u) continue;
+            if (ld_cg(a.ctrl + 1) != 0u) { fine = 0u; break; }
             if (clock64() - t0 > a.timeout_cycles) {
                 atomicExch(a.ctrl + 1, 1u);
                 fine = 0u;
                 break;
             }
         }
-        __threadfence();
         s.fine = fine;
     }
     ++epoch;
@@ -249,6 +254,13 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
     uint32_t epoch = 0;
     bool ok = gw_sync(s, a, epoch);
     mark_phase(4);
+    // bit k: the window entry tid + k * kBlock this thread gathers is one of
+    // this CTA's rows (entries lb + r * G)
+    uint32_t own = 0;
+    for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k) {
+        const uint32_t e = tid + k * kBlock;
+        if (e >= lb && (e - lb) % G == 0u) own |= 1u << k;
+    }
 
     // ORs this CTA's share of the balls of ax[0..nacc) into the bitmap.  The
     // (ball word, codeword) pairs are taken ball-word-major, so the lanes of
@@ -341,6 +353,13 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         // the bitmap (complete up to window t-2)
         emit_prev();
         mark_phase(0);
+        if (a.early) {
+            // window t-1's balls, complete at this phase's barrier: the rows
+            // of window t are probed against them in phase B
+            mark_begin(nprev);
+            mark_some(mark_left());
+            mark_phase(2);
+        }
         {
             const uint64_t chunk = (span + G - 1) / G;
             const uint64_t c0 = min(R0 + (uint64_t)lb * chunk, R0 + span);
@@ -362,13 +381,13 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                             // in the word, or this bit of a word one high bit away
                             bool hit = (ld_cg(a.bitmap + w0) & s.lowball[1][b]) != 0u;
                             const int nh = n > 5 ? n - 5 : 0;
-                            for (int j0 = 0; j0 < nh && !hit; j0 += 8) {
-                                uint32_t v[8];
+                            for (int j0 = 0; j0 < nh && !hit; j0 += kGwProbeBatch) {
+                                uint32_t v[kGwProbeBatch];
 #pragma unroll
-                                for (int u = 0; u < 8; ++u)
+                                for (int u = 0; u < kGwProbeBatch; ++u)
                                     v[u] = j0 + u < nh ? ld_cg(a.bitmap + (w0 ^ (1u << (j0 + u)))) : 0u;
 #pragma unroll
-                                for (int u = 0; u < 8; ++u) hit = hit || ((v[u] >> b) & 1u);
+                                for (int u = 0; u < kGwProbeBatch; ++u) hit = hit || ((v[u] >> b) & 1u);
                             }
                             keep = !hit;
                         }
@@ -399,23 +418,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             __syncthreads();
         }
         const uint32_t Suse = min(S, (uint32_t)kGwSurvCap);
-        if (tid == 0) {
-            uint64_t rn = R0 + span;
-            if (S > (uint32_t)kGwSurvCap) {
-                // the window ends after its kGwSurvCap-th survivor, which
-                // sits in the segment of the last CTA g with pref[g] <= it
-                const uint32_t e = (uint32_t)kGwSurvCap - 1u;
-                uint32_t lo = 0, hi = G;
-                while (hi - lo > 1u) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s.pref[mid] <= e) lo = mid;
-                    else hi = mid;
-                }
-                rn = R0 + ld_cg(a.seg_off + ((size_t)p * G + lo) * kGwChunk + (e - s.pref[lo])) + 1;
-            }
-            s.bs.bcast64 = rn;
-            s.npairs = 0;
-        }
+        if (tid == 0) s.npairs = 0;
         // entry e of the window sits in the segment of the last CTA g with
         // pref[g] <= e (empty segments share their successor's prefix)
         {
@@ -439,38 +442,67 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                     vo[k] = ld_cg(a.seg_off + at[k]);
                 }
 #pragma unroll
-            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k)
-                if (tid + k * kBlock < Suse) {
-                    s.wx[tid + k * kBlock] = vx[k];
-                    s.woff[tid + k * kBlock] = vo[k];
+            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k) {
+                const uint32_t e = tid + k * kBlock;
+                if (e < Suse) {
+                    s.wx[e] = vx[k];
+                    s.woff[e] = vo[k];
+                    // this CTA's rows also go to acc, contiguous
+                    if ((own >> k) & 1u) s.acc[(e - lb) / G] = vx[k];
                 }
+            }
         }
         // this CTA's rows: entries lb + r * G, r < rows; s.flags[r] = killed
         const uint32_t rows = Suse > lb ? (Suse - lb + G - 1) / G : 0u;
         for (uint32_t r = tid; r < rows; r += kBlock) s.flags[r] = 0;
         __syncthreads();
-        const uint64_t Rnext = s.bs.bcast64;
+        // a window over kGwSurvCap survivors ends after the last one taken
+        const uint64_t Rnext = S > (uint32_t)kGwSurvCap ? R0 + s.woff[kGwSurvCap - 1] + 1 : R0 + span;
         mark_phase(5);
         {
-            // window t-1's marks, spread over the tests below: a slice after
-            // each column of them, the rest at the end
-            mark_begin(nprev);
+            if (a.early) {
+                // the bitmap holds every earlier window's balls: a row meets
+                // a previous accept iff a marked vector is within distance 1
+                // of it.  One warp per row, lane j < n - 5 probing the word
+                // one high bit j away, lane 31 the row's own word.
+                const int nh = n > 5 ? n - 5 : 0;
+                for (uint32_t r = warp_id(); r < rows; r += kWarps) {
+                    const uint32_t x = s.acc[r];
+                    const uint32_t key = a.reversed ? reverse_n(x, n) : x;
+                    const uint32_t w0 = key >> 5, b = key & 31u;
+                    bool hit = false;
+                    if (lane < nh) hit = ((ld_cg(a.bitmap + (w0 ^ (1u << lane))) >> b) & 1u) != 0u;
+                    else if (lane == 31) hit = (ld_cg(a.bitmap + w0) & s.lowball[1][b]) != 0u;
+                    hit = __any_sync(kFull, hit);
+                    if (lane == 0) s.flags[r] = hit ? 1 : 0;
+                }
+                mark_begin(0);
+                mark_phase(3);
+            } else {
+                // window t-1's marks, spread over the tests below: a slice
+                // after each column of them, the rest at the end
+                mark_begin(nprev);
+            }
             const uint32_t mslice = (mark_left() + 7u) / 8u;
+            const uint32_t* rx = s.acc;   // this CTA's rows, contiguous
             // the previous window's accepts against every row
-            for (uint32_t c = tid; c < nprev; c += kBlock) {
+            for (uint32_t c = tid; c < (a.early ? 0u : nprev); c += kBlock) {
                 mark_some(mslice);
                 const uint32_t y = s.ax[c];
                 uint32_t r = 0;
                 for (; r + 4 <= rows; r += 4) {
-                    const uint32_t x0 = s.wx[lb + r * G], x1 = s.wx[lb + (r + 1) * G];
-                    const uint32_t x2 = s.wx[lb + (r + 2) * G], x3 = s.wx[lb + (r + 3) * G];
-                    if (popc(x0 ^ y) < d) s.flags[r] = 1;
-                    if (popc(x1 ^ y) < d) s.flags[r + 1] = 1;
-                    if (popc(x2 ^ y) < d) s.flags[r + 2] = 1;
-                    if (popc(x3 ^ y) < d) s.flags[r + 3] = 1;
+                    const uint4 q = *reinterpret_cast<const uint4*>(rx + r);
+                    const int m0 = popc(q.x ^ y), m1 = popc(q.y ^ y);
+                    const int m2 = popc(q.z ^ y), m3 = popc(q.w ^ y);
+                    if (min(min(m0, m1), min(m2, m3)) < d) {
+                        if (m0 < d) s.flags[r] = 1;
+                        if (m1 < d) s.flags[r + 1] = 1;
+                        if (m2 < d) s.flags[r + 2] = 1;
+                        if (m3 < d) s.flags[r + 3] = 1;
+                    }
                 }
                 for (; r < rows; ++r)
-                    if (popc(s.wx[lb + r * G] ^ y) < d) s.flags[r] = 1;
+                    if (popc(rx[r] ^ y) < d) s.flags[r] = 1;
                 my_tests += rows;
             }
             // the window's entries against the later rows: pairs (k, i).
@@ -484,13 +516,26 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 if (k >= Suse) continue;
                 const uint32_t y = s.wx[k];
                 const uint32_t r0 = k < lb ? 0u : (k - lb) / G + 1u;
-                for (uint32_t r = r0; r < rows; ++r) {
-                    const uint32_t i = lb + r * G;
-                    if (popc(s.wx[i] ^ y) < d) {
-                        const uint32_t e = atomicAdd(&s.npairs, 1u);
-                        if (e < kGwPairCap) s.u.pairs[e] = (k << 16) | i;
+                auto pair = [&](uint32_t r) {
+                    const uint32_t e = atomicAdd(&s.npairs, 1u);
+                    if (e < kGwPairCap) s.u.pairs[e] = (k << 16) | (lb + r * G);
+                };
+                uint32_t r = r0;
+                for (; r < rows && (r & 3u); ++r)
+                    if (popc(rx[r] ^ y) < d) pair(r);
+                for (; r + 4 <= rows; r += 4) {
+                    const uint4 q = *reinterpret_cast<const uint4*>(rx + r);
+                    const int m0 = popc(q.x ^ y), m1 = popc(q.y ^ y);
+                    const int m2 = popc(q.z ^ y), m3 = popc(q.w ^ y);
+                    if (min(min(m0, m1), min(m2, m3)) < d) {
+                        if (m0 < d) pair(r);
+                        if (m1 < d) pair(r + 1);
+                        if (m2 < d) pair(r + 2);
+                        if (m3 < d) pair(r + 3);
                     }
                 }
+                for (; r < rows; ++r)
+                    if (popc(rx[r] ^ y) < d) pair(r);
                 if (rows > r0) my_tests += rows - r0;
             }
             mark_some(mark_left());
@@ -586,6 +631,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             __syncthreads();
             nacc = gw_pair_rounds(s, Suse, P, R0, &rounds_total);
             ++pair_windows;
+            mark_phase(9);
         } else {
             // drop the entries a previous accept rejects, then the conflict
             // matrices
@@ -601,6 +647,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             }
             __syncthreads();
             ++fallbacks;
+            mark_phase(10);
         }
         mark_phase(8);
         Kprev = K;
@@ -728,11 +775,14 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     };
     if ((e = cudaMemsetAsync(ws + L.off_ctrl, 0, 256, s)) != cudaSuccess)
         return cuda_fail("control words");
-    // d >= 4: marks of radius d-2 and lookups that probe radius 1 (a
-    // candidate within d-1 of a codeword is within 1 of a vector within d-2
-    // of it); the ball to mark is several times smaller
+    // default: early marks with radius-(d-2) balls and radius-1 probes.
+    // GC_GRID_EARLY=0 marks during the row tests instead (radius d-2 for
+    // d >= 4, d-1 below, unless GC_GRID_PROBE says otherwise)
     uint32_t probe = p.d >= 4 ? 1u : 0u;
     if (const char* e = std::getenv("GC_GRID_PROBE")) probe = std::atoi(e) != 0 && p.d >= 2 ? 1u : 0u;
+    uint32_t early = p.d >= 2 ? 1u : 0u;
+    if (const char* e = std::getenv("GC_GRID_EARLY")) early = std::atoi(e) != 0 && p.d >= 2 ? 1u : 0u;
+    if (early) probe = 1u;
     const int rad = p.d - 1 - (int)probe;
     const uint32_t hl = (uint32_t)high_ball_len(p.n, rad + 1);
     const int nh = p.n > 5 ? p.n - 5 : 0;
@@ -769,6 +819,7 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     a.extra_arrivals = fault ? 1u : 0u;
     a.reversed = p.ord == GC_ORDER_GREVLEX ? 1u : 0u;
     a.probe = probe;
+    a.early = early;
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel((const void*)grid_sweep_kernel, dim3(L.grid), dim3(kBlock),
                                     args, L.smem_bytes, s);

@@ -174,26 +174,35 @@ def test_grid_strategy_mid_and_weighted(o, n, d, w):
     assert st.strategy == G().STRATEGY_BITMAP_GRID and st.codewords == len(want)
 
 
-@pytest.mark.parametrize("probe", ["0", "1"])
-def test_grid_radius_split_both_ways(probe, monkeypatch):
+@pytest.mark.parametrize("env", [{"GC_GRID_PROBE": "0"}, {"GC_GRID_PROBE": "1"},
+                                 {"GC_GRID_EARLY": "1"}, {"GC_GRID_EARLY": "0"}])
+def test_grid_radius_split_both_ways(env, monkeypatch):
     """The grid sweep either marks radius-(d-1) balls and looks up one bit,
-    or (the default for d >= 4) marks radius-(d-2) balls and probes the
-    candidate's radius-1 neighbourhood; GC_GRID_PROBE forces either.  Both
-    give the oracle's code, in every order, with and without a weight."""
-    monkeypatch.setenv("GC_GRID_PROBE", probe)
+    or marks radius-(d-2) balls and probes the candidate's radius-1
+    neighbourhood; with early marks, window t-1's balls go into the bitmap
+    before window t's rows are probed against it instead of tested against
+    window t-1's accepts.  GC_GRID_PROBE / GC_GRID_EARLY force each form.
+    All give the oracle's code, in every order, with and without a weight."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
     for n, d, o, w in [(18, 3, "lex", -1), (19, 4, "gray", -1), (20, 4, "grevlex", -1),
                        (20, 5, "grlex", -1), (21, 6, "lex", -1), (18, 4, "grevlex", 7),
-                       (20, 4, "gray", 9), (9, 4, "lex", -1), (5, 3, "grlex", -1)]:
+                       (20, 4, "gray", 9), (9, 4, "lex", -1), (5, 3, "grlex", -1),
+                       (20, 3, "grevlex", -1), (19, 3, "gray", 6), (4, 2, "lex", -1)]:
         got, st = gpu_code(n, d, o, w, "grid")
-        assert got.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (probe, n, d, o, w)
+        assert got.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (env, n, d, o, w)
 
 
-def test_grid_strategy_on_fewer_ctas():
-    """The grid strategy on a grid of 1, 2 and 7 CTAs (many rows per CTA)."""
-    want = oracle.greedy_ball(20, 4, "grlex")
-    for grid in (1, 2, 7):
-        got, _ = gpu_code(20, 4, "grlex", -1, "grid", grid=grid)
-        assert got.tolist() == want.tolist(), grid
+@pytest.mark.parametrize("early", ["0", "1"])
+def test_grid_strategy_on_fewer_ctas(early, monkeypatch):
+    """The grid strategy on a grid of 1, 2 and 7 CTAs (many rows per CTA),
+    with window t-1's balls marked during the tests or before the rows."""
+    monkeypatch.setenv("GC_GRID_EARLY", early)
+    for n, d, o in [(20, 4, "grlex"), (19, 3, "lex")]:
+        want = oracle.greedy_ball(n, d, o)
+        for grid in (1, 2, 7):
+            got, _ = gpu_code(n, d, o, -1, "grid", grid=grid)
+            assert got.tolist() == want.tolist(), (n, d, o, grid)
 
 
 # (n, d, order, strategy, survivor target, whether pair lists must decide
