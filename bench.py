@@ -429,7 +429,10 @@ def run_ours(args):
     marks_per_s = marks / (mean_step_ms * 1e-3)
     chain_us = {name(c): 1e3 * per_code_ms[name(c)] / max(s.windows, 1)
                 for c, s in zip(WORKLOAD, stats)}
-    traffic_launch = recorded_traffic("grid_sweep_n31d3_lex_dram.md", GRID_SOURCES)
+    # DRAM bytes per grid-sweep launch, averaged over the nine codes (one
+    # 1-pass ncu capture of the whole step); only for the full workload
+    traffic_launch = (None if args.only else
+                      recorded_traffic("grid_sweep_bench_workload_dram.md", GRID_SOURCES))
 
     extra = {}
     if not args.only and not args.no_extras:
