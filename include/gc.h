@@ -149,7 +149,12 @@ typedef struct {
      * [6] resolving (a pipelined job's generator CTAs: searching the window's
      * conflicting pairs), [7] committing; within [6]: [8] conflict matrix or
      * bucketed search, [9] resolution rounds, [10] appending and the kill
-     * step; [11] counts resolution rounds (not cycles). */
+     * step; [11] counts resolution rounds (not cycles).  The grid bitmap
+     * sweep (GC_STRATEGY_BITMAP_GRID) uses them as: [0] output of the
+     * previous window's accepts, [1] generation and bitmap probes, [2] ball
+     * marks, [3] row probes, [4] grid barriers, [5] gather, [6] pair tests,
+     * [7] publishing kills and pairs, [8] deciding windows without pairs,
+     * [9] with pair rounds, [10] with conflict matrices; [11] rounds. */
     uint64_t phase_cycles[12];
     /* Pipelined bitmap jobs in large groups: windows decided from the list
      * of their conflicting pairs that the group's generator CTAs found, and

@@ -55,11 +55,13 @@ constexpr int kGwSurvCap = 4096;        // survivors decided per window
 constexpr int kGwChunk = 4096;          // candidates per CTA per window
 constexpr uint32_t kGwPairCap = 2048;   // pairs one CTA may list per window
 constexpr uint32_t kGwPairSmem = 16384; // pairs a CTA takes into shared memory
+constexpr uint32_t kGwPairGlobal = 8 * kGwPairSmem;  // pairs decided by rounds over L2
 constexpr int kGwMaxCtas = kBlock;      // one count per thread in the prefix scans
 constexpr int kGwProbeBatch = 14;       // high-bit probes a lookup issues at once
 static_assert(kGwSurvCap <= 65536, "pairs pack two entry indices in 16 bits each");
 static_assert(kGwSurvCap == 4 * kBlock, "the accept compaction gives a thread four entries");
 static_assert(kGwPairCap <= kGwPairSmem, "a CTA's own pairs are staged in the pair area");
+static_assert(kGwPairCap <= 2 * kBlock, "a thread publishes at most two of its CTA's pairs");
 
 struct GwArgs {
     Order ord;
@@ -74,15 +76,18 @@ struct GwArgs {
     uint32_t* seg_off;        // [2][grid][kGwChunk] their offsets from the window start
     uint32_t* slot;           // [2][grid] survivor counts
     uint32_t* pslot;          // [2][grid] pair counts (kGwPairCap + 1: overflow)
-    uint32_t* pairbuf;        // [grid][kGwPairCap] (earlier << 16) | later
+    uint32_t* pairbuf;        // grid * kGwPairCap: the window's pairs, (earlier << 16) | later,
+                              // packed in the order the CTAs reserve space (ctrl[2 + parity])
     uint8_t* killbuf;         // [kGwSurvCap] 1: the entry meets a previous accept
-    unsigned* ctrl;           // [0] barrier arrivals, [1] error word
+    unsigned* ctrl;           // [0] barrier arrivals, [1] error word, [2..3] pairs listed
+                              // in the window of parity 0 / 1
     uint32_t wmin, wmax, target;
     long long timeout_cycles;
     uint32_t timing_cta;
     uint32_t extra_arrivals;  // fault injection: barriers wait for this many CTAs more
     uint32_t reversed;        // 1: the bitmap is indexed by the bit-reversed vector
     uint32_t probe;           // 1: radius-(d-2) balls marked, lookups probe radius 1
+    uint32_t pair_smem;       // pairs decided from shared memory (<= kGwPairSmem)
     uint32_t early;           // 1 (with probe): window t-1's balls marked in phase A of
                               // window t, rows probed in phase B instead of tested
 };
@@ -194,6 +199,90 @@ __device__ uint32_t gw_pair_rounds(GwSmem& s, uint32_t n, uint32_t P, uint64_t R
                             keep ? (uint32_t)(R0 + s.woff[i]) : 0u, s.ax, s.ax_off, nacc);
     }
     return nacc;
+}
+
+// CTA-wide.  Rounds as in gw_pair_rounds, over a pair list too long for
+// shared memory, read from the global list pairs[0..P) in every round; a
+// round counts the pairs still relevant (later entry undecided, earlier
+// entry not rejected).  Once they fit in shared memory (fit <= kGwPairSmem)
+// a last pass copies them there and returns their number, for gw_pair_rounds
+// to carry on from.  Returns 0 once every entry is decided.  Counts rounds in
+// *rounds.
+__device__ uint32_t gw_pair_rounds_global(GwSmem& s, const uint32_t* pairs, uint32_t P, uint32_t n,
+                                          uint32_t fit, uint64_t* rounds) {
+    constexpr uint32_t kNone = 0xffffffffu;   // pairs are below 2^28
+    constexpr uint32_t kDepth = 8;            // loads in flight per thread
+    uint8_t* killed = s.flags;
+    uint8_t* blocked = s.flags + kGwSurvCap;
+    const int lane = lane_id();
+    for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
+        killed[i] = 0;
+        blocked[i] = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        ++*rounds;
+        uint32_t cnt = 0;
+        for (uint32_t e0 = 0; e0 < P; e0 += kDepth * kBlock) {
+            uint32_t pr[kDepth];
+#pragma unroll
+            for (uint32_t u = 0; u < kDepth; ++u) {
+                const uint32_t e = e0 + u * kBlock + threadIdx.x;
+                pr[u] = e < P ? ld_cg(pairs + e) : kNone;
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < kDepth; ++u) {
+                if (pr[u] == kNone) continue;
+                const uint32_t k = pr[u] >> 16, i = pr[u] & 0xffffu;
+                if (s.state[i] != 0) continue;
+                const uint8_t sk = s.state[k];
+                if (sk == 1) { killed[i] = 1; ++cnt; }
+                else if (sk == 0) { blocked[i] = 1; ++cnt; }
+            }
+        }
+        uint32_t R = 0;
+        block_exclusive_scan(s.bs, cnt, &R);   // ends with a CTA barrier
+        bool left = false;
+        for (uint32_t i = threadIdx.x; i < n; i += kBlock)
+            if (s.state[i] == 0) {
+                if (killed[i]) s.state[i] = 2;
+                else if (!blocked[i]) s.state[i] = 1;
+                else left = true;
+                killed[i] = 0;
+                blocked[i] = 0;
+            }
+        if (!__syncthreads_or(left)) return 0u;
+        if (R > fit) continue;
+        // the pairs relevant now are among the R counted above: copy them
+        if (threadIdx.x == 0) s.npairs = 0;
+        __syncthreads();
+        for (uint32_t e0 = 0; e0 < P; e0 += kDepth * kBlock) {
+            uint32_t pr[kDepth];
+#pragma unroll
+            for (uint32_t u = 0; u < kDepth; ++u) {
+                const uint32_t e = e0 + u * kBlock + threadIdx.x;
+                pr[u] = e < P ? ld_cg(pairs + e) : kNone;
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < kDepth; ++u) {
+                bool rel = false;
+                if (pr[u] != kNone) {
+                    const uint32_t k = pr[u] >> 16, i = pr[u] & 0xffffu;
+                    rel = s.state[i] == 0 && s.state[k] != 2;
+                }
+                const unsigned bal = __ballot_sync(kFull, rel);
+                uint32_t base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&s.npairs, (uint32_t)__popc(bal));
+                base = __shfl_sync(kFull, base, 0);
+                if (rel) {
+                    const uint32_t q = base + __popc(bal & ((1u << lane) - 1u));
+                    if (q < kGwPairSmem) s.u.pairs[q] = pr[u];
+                }
+            }
+        }
+        __syncthreads();
+        return min(s.npairs, (uint32_t)kGwPairSmem);
+    }
 }
 
 __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_constant__ GwArgs a) {
@@ -409,6 +498,9 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         mark_phase(4);
 
         // ---- B: gather the window, test this CTA's rows
+        // (every CTA has read the pair count of window t-1 before this
+        // phase's barrier; window t+1 adds to it after the next one)
+        if (lb == 0 && tid == 0) atomicExch(a.ctrl + 2 + (p ^ 1), 0u);
         uint32_t S = 0;
         {
             const uint32_t v = (uint32_t)tid < G ? ld_cg(a.slot + (size_t)p * G + tid) : 0u;
@@ -505,77 +597,122 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                     if (popc(rx[r] ^ y) < d) s.flags[r] = 1;
                 my_tests += rows;
             }
-            // the window's entries against the later rows: pairs (k, i).
-            // Entry k meets the rows after it, so a thread takes columns from
-            // both ends of each half of the window (tid, 2047 - tid, 2048 +
-            // tid, 4095 - tid) and every thread has about the same tests.
-#pragma unroll 1
-            for (uint32_t m = 0; m < (uint32_t)kGwSurvCap / kBlock; ++m) {
-                const uint32_t k = (m & 1u) ? kBlock * (m + 1u) - 1u - tid : kBlock * m + tid;
-                mark_some(mslice);
-                if (k >= Suse) continue;
-                const uint32_t y = s.wx[k];
-                const uint32_t r0 = k < lb ? 0u : (k - lb) / G + 1u;
-                auto pair = [&](uint32_t r) {
-                    const uint32_t e = atomicAdd(&s.npairs, 1u);
-                    if (e < kGwPairCap) s.u.pairs[e] = (k << 16) | (lb + r * G);
-                };
-                uint32_t r = r0;
-                for (; r < rows && (r & 3u); ++r)
-                    if (popc(rx[r] ^ y) < d) pair(r);
-                for (; r + 4 <= rows; r += 4) {
-                    const uint4 q = *reinterpret_cast<const uint4*>(rx + r);
-                    const int m0 = popc(q.x ^ y), m1 = popc(q.y ^ y);
-                    const int m2 = popc(q.z ^ y), m3 = popc(q.w ^ y);
-                    if (min(min(m0, m1), min(m2, m3)) < d) {
-                        if (m0 < d) pair(r);
-                        if (m1 < d) pair(r + 1);
-                        if (m2 < d) pair(r + 2);
-                        if (m3 < d) pair(r + 3);
+            auto pair = [&](uint32_t k, uint32_t i) {
+                const uint32_t e = atomicAdd(&s.npairs, 1u);
+                if (e < kGwPairCap) s.u.pairs[e] = (k << 16) | i;
+            };
+            if (a.early) {
+                // the window's entries against the later rows: pairs (k, i),
+                // k < i.  Row r (entry i_r = lb + r * G) meets the i_r entries
+                // before it; the (row, entry) triangle, flattened row by row
+                // (tri(r) tests before row r), is cut into one equal span per
+                // warp, whose lanes sweep consecutive entries, four to a
+                // 16-byte load, against the row word held by the whole warp.
+                auto tri = [&](uint32_t r) { return r * lb + G * (r * (r - 1u) / 2u); };
+                const uint32_t T = tri(rows), w = warp_id();
+                const uint32_t p0 = (uint32_t)((uint64_t)T * w / kWarps);
+                const uint32_t p1 = (uint32_t)((uint64_t)T * (w + 1u) / kWarps);
+                if (p0 < p1) {
+                    uint32_t lo = 0, hi = rows;   // tri(lo) <= p0 < tri(hi)
+                    while (hi - lo > 1u) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (tri(mid) <= p0) lo = mid;
+                        else hi = mid;
+                    }
+                    uint32_t r = lo, pos = p0;
+                    while (pos < p1) {
+                        const uint32_t i = lb + r * G, x = rx[r];
+                        const uint32_t ka = pos - tri(r);
+                        const uint32_t kb = min(i, ka + (p1 - pos));
+                        for (uint32_t k0 = ka & ~127u; k0 < kb; k0 += 128u) {
+                            const uint32_t k = k0 + 4u * (uint32_t)lane;
+                            const uint4 q = *reinterpret_cast<const uint4*>(s.wx + k);
+                            int m0 = popc(q.x ^ x), m1 = popc(q.y ^ x);
+                            int m2 = popc(q.z ^ x), m3 = popc(q.w ^ x);
+                            if (k0 < ka || k0 + 128u > kb) {   // entries outside [ka, kb)
+                                if (k < ka || k >= kb) m0 = 32;
+                                if (k + 1u < ka || k + 1u >= kb) m1 = 32;
+                                if (k + 2u < ka || k + 2u >= kb) m2 = 32;
+                                if (k + 3u < ka || k + 3u >= kb) m3 = 32;
+                            }
+                            if (min(min(m0, m1), min(m2, m3)) < d) {
+                                if (m0 < d) pair(k, i);
+                                if (m1 < d) pair(k + 1u, i);
+                                if (m2 < d) pair(k + 2u, i);
+                                if (m3 < d) pair(k + 3u, i);
+                            }
+                        }
+                        if (lane == 0) my_tests += kb - ka;
+                        pos += kb - ka;
+                        ++r;
                     }
                 }
-                for (; r < rows; ++r)
-                    if (popc(rx[r] ^ y) < d) pair(r);
-                if (rows > r0) my_tests += rows - r0;
+            } else {
+                // the window's entries against the later rows, a thread per
+                // entry (column) with window t-1's marks between them.  Entry
+                // k meets the rows after it, so a thread takes columns from
+                // both ends of each half of the window (tid, 2047 - tid,
+                // 2048 + tid, 4095 - tid) and every thread has about the same
+                // tests.
+#pragma unroll 1
+                for (uint32_t m = 0; m < (uint32_t)kGwSurvCap / kBlock; ++m) {
+                    const uint32_t k = (m & 1u) ? kBlock * (m + 1u) - 1u - tid : kBlock * m + tid;
+                    mark_some(mslice);
+                    if (k >= Suse) continue;
+                    const uint32_t y = s.wx[k];
+                    const uint32_t r0 = k < lb ? 0u : (k - lb) / G + 1u;
+                    uint32_t r = r0;
+                    for (; r < rows && (r & 3u); ++r)
+                        if (popc(rx[r] ^ y) < d) pair(k, lb + r * G);
+                    for (; r + 4 <= rows; r += 4) {
+                        const uint4 q = *reinterpret_cast<const uint4*>(rx + r);
+                        const int m0 = popc(q.x ^ y), m1 = popc(q.y ^ y);
+                        const int m2 = popc(q.z ^ y), m3 = popc(q.w ^ y);
+                        if (min(min(m0, m1), min(m2, m3)) < d) {
+                            if (m0 < d) pair(k, lb + r * G);
+                            if (m1 < d) pair(k, lb + (r + 1) * G);
+                            if (m2 < d) pair(k, lb + (r + 2) * G);
+                            if (m3 < d) pair(k, lb + (r + 3) * G);
+                        }
+                    }
+                    for (; r < rows; ++r)
+                        if (popc(rx[r] ^ y) < d) pair(k, lb + r * G);
+                    if (rows > r0) my_tests += rows - r0;
+                }
             }
             mark_some(mark_left());
             __syncthreads();
+            mark_phase(6);
             // publish: the kills, and the pairs whose later entry survived
             for (uint32_t r = tid; r < rows; r += kBlock) a.killbuf[lb + r * G] = s.flags[r];
             const uint32_t np = s.npairs;
             uint32_t kept = 0;
             if (np <= kGwPairCap) {
-                uint32_t* pb = a.pairbuf + (size_t)lb * kGwPairCap;
-                for (uint32_t t0 = 0; t0 < np; t0 += kBlock) {
-                    const uint32_t e = t0 + tid;
-                    const uint32_t pr = e < np ? s.u.pairs[e] : 0u;
-                    const bool keep = e < np && s.flags[((pr & 0xffffu) - lb) / G] == 0;
-                    // block_append would reorder nothing here either; the
-                    // pairs' order does not matter, their count does
-                    const unsigned bal = __ballot_sync(kFull, keep);
-                    if (lane == 0) s.bs.warp_sum[warp_id()] = __popc(bal);
-                    __syncthreads();
-                    if (warp_id() == 0) {
-                        const uint32_t wv = lane < kWarps ? s.bs.warp_sum[lane] : 0u;
-                        uint32_t incl = wv;
-#pragma unroll
-                        for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                            const uint32_t tv = __shfl_up_sync(kFull, incl, o2);
-                            if (lane >= o2) incl += tv;
-                        }
-                        if (lane < kWarps) s.bs.warp_sum[lane] = incl - wv;
-                        if (lane == 31) s.bs.warp_sum[kWarps] = incl;
-                    }
-                    __syncthreads();
-                    if (keep)
-                        pb[kept + s.bs.warp_sum[warp_id()] + __popc(bal & ((1u << lane) - 1u))] = pr;
-                    kept += s.bs.warp_sum[kWarps];
-                    __syncthreads();
+                // the pairs whose later entry survived go to the window's
+                // list, at an offset reserved on its counter (the pairs'
+                // order does not matter, their count does)
+                uint32_t pr0 = 0, pr1 = 0;
+                bool k0 = false, k1 = false;
+                if ((uint32_t)tid < np) {
+                    pr0 = s.u.pairs[tid];
+                    k0 = s.flags[((pr0 & 0xffffu) - lb) / G] == 0;
+                }
+                if ((uint32_t)tid + kBlock < np) {
+                    pr1 = s.u.pairs[tid + kBlock];
+                    k1 = s.flags[((pr1 & 0xffffu) - lb) / G] == 0;
+                }
+                uint32_t pos = block_exclusive_scan(s.bs, (uint32_t)k0 + (uint32_t)k1, &kept);
+                if (tid == 0 && kept) s.bs.bcast64 = atomicAdd(a.ctrl + 2 + p, kept);
+                __syncthreads();
+                if (kept) {
+                    const uint32_t base = (uint32_t)s.bs.bcast64;
+                    if (k0) a.pairbuf[base + pos++] = pr0;
+                    if (k1) a.pairbuf[base + pos] = pr1;
                 }
             }
             if (tid == 0) a.pslot[(size_t)p * G + lb] = np <= kGwPairCap ? kept : kGwPairCap + 1u;
         }
-        mark_phase(6);
+        mark_phase(7);
         ok = gw_sync(s, a, epoch);
         if (!ok) break;
         mark_phase(4);
@@ -596,13 +733,11 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             for (uint32_t k = 0; k < 4; ++k)
                 if (e0 + k < Suse) s.state[e0 + k] = ((kw >> (8 * k)) & 0xffu) ? 2 : 0;
         }
-        uint32_t P = 0;
-        {
-            const uint32_t ex = block_exclusive_scan(s.bs, min(v, kGwPairCap), &P);
-            if ((uint32_t)tid < G) s.pref[tid] = ex;
-        }
-        const bool over =
-            __syncthreads_or((uint32_t)tid < G && v > kGwPairCap) || P > kGwPairSmem;
+        const uint32_t P = ld_cg(a.ctrl + 2 + p);
+        // a CTA's list overflowed, or the window's is too long for rounds
+        // over L2: the conflict matrices
+        const bool over = __syncthreads_or((uint32_t)tid < G && v > kGwPairCap) ||
+                          P > kGwPairGlobal;
         uint32_t nacc = 0;
         if (!over && P == 0u) {
             // no conflict inside the window: the entries no previous accept
@@ -622,14 +757,15 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 }
             __syncthreads();
         } else if (!over) {
-            for (uint32_t g = warp_id(); g < G; g += kWarps) {
-                const uint32_t p0 = s.pref[g];
-                const uint32_t c = min(ld_cg(a.pslot + (size_t)p * G + g), kGwPairCap);
-                const uint32_t* src = a.pairbuf + (size_t)g * kGwPairCap;
-                for (uint32_t q = lane; q < c; q += 32) s.u.pairs[p0 + q] = ld_cg(src + q);
+            uint32_t Ps = P;
+            if (P <= a.pair_smem) {
+                for (uint32_t e = tid; e < P; e += kBlock) s.u.pairs[e] = ld_cg(a.pairbuf + e);
+                __syncthreads();
+            } else {
+                // too many for shared memory: the first rounds from L2
+                Ps = gw_pair_rounds_global(s, a.pairbuf, P, Suse, a.pair_smem, &rounds_total);
             }
-            __syncthreads();
-            nacc = gw_pair_rounds(s, Suse, P, R0, &rounds_total);
+            nacc = gw_pair_rounds(s, Suse, Ps, R0, &rounds_total);
             ++pair_windows;
             mark_phase(9);
         } else {
@@ -671,7 +807,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
     // the last window's accepts go to the output
     if (ok) {
         emit_prev();
-        mark_phase(7);
+        mark_phase(0);
     }
     // statistics: warp-reduce, one atomic per warp
     uint64_t tt = my_tests, m = my_marks, dn = dense;
@@ -820,6 +956,11 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     a.reversed = p.ord == GC_ORDER_GREVLEX ? 1u : 0u;
     a.probe = probe;
     a.early = early;
+    // GC_GRID_PAIR_SMEM (tests): decide windows of more pairs through the
+    // rounds over the global list
+    a.pair_smem = kGwPairSmem;
+    if (const char* e = std::getenv("GC_GRID_PAIR_SMEM"))
+        a.pair_smem = (uint32_t)std::max(1, std::min((int)kGwPairSmem, std::atoi(e)));
     void* args[] = {&a};
     e = cudaLaunchCooperativeKernel((const void*)grid_sweep_kernel, dim3(L.grid), dim3(kBlock),
                                     args, L.smem_bytes, s);

@@ -193,6 +193,19 @@ def test_grid_radius_split_both_ways(env, monkeypatch):
         assert got.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (env, n, d, o, w)
 
 
+@pytest.mark.parametrize("cap", ["1", "40", "700"])
+def test_grid_long_pair_lists_from_l2(cap, monkeypatch):
+    """Windows whose pair list exceeds what shared memory takes run their
+    first rounds over the list in L2, then carry on in shared memory;
+    GC_GRID_PAIR_SMEM lowers that limit so small codes take the path."""
+    monkeypatch.setenv("GC_GRID_PAIR_SMEM", cap)
+    for n, d, o, w in [(20, 3, "lex", -1), (21, 3, "gray", -1), (20, 4, "grlex", -1),
+                       (20, 3, "grevlex", -1), (19, 5, "lex", -1), (18, 3, "grlex", 6)]:
+        got, st = gpu_code(n, d, o, w, "grid")
+        assert got.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (cap, n, d, o, w)
+        assert st.pair_windows > 0
+
+
 @pytest.mark.parametrize("early", ["0", "1"])
 def test_grid_strategy_on_fewer_ctas(early, monkeypatch):
     """The grid strategy on a grid of 1, 2 and 7 CTAs (many rows per CTA),
