@@ -192,6 +192,9 @@ struct __align__(16) SweepSmem {
     GroupDesc grp;
     uint32_t slice_cnt[kMaxSlices];  // distance jobs: survivors per local slice
     unsigned long long phase[12];  // phase timers (thread 0 of the group's first CTA)
+    // the current job's windows, survivors, pair-decided and pair-overflow
+    // windows: kept by thread 0 (uniform values, out of the registers)
+    unsigned long long jstat[4];
     long long tprev;
     BlockScratch bs;
     __align__(16) uint32_t dund[kDenseWords];  // whole-window resolver: undecided /
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
         Word* prev = s.accB;
         uint32_t nprev = 0;
         uint64_t my_tests = 0, my_marks = 0, dense = 0, resolve_tests = 0;
-        uint64_t windows = 0, surv_total = 0;
+        if (tid == 0) s.jstat[0] = s.jstat[1] = s.jstat[2] = s.jstat[3] = 0;
         if (timing)
             for (int k = 0; k < 12; ++k) s.phase[k] = 0;
         // adds the cycles since the last mark to phase k (first CTA, thread 0)
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
             }
         };
         // resolves the gathered window in order with conflict matrices
-        uint64_t pair_done = 0, pair_failed = 0;  // windows decided from pair lists
+
         auto resolve = [&](uint32_t Suse, uint64_t& rt) -> uint32_t {
             return job.orth ? block_resolve<true>(s.bs, s.list_x, s.list_off, s.dead, Suse, d, cur,
                                                   s.acc_off, s.M, rt,
@@ -731,9 +734,9 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                                     reinterpret_cast<uint8_t*>(&s.M[0][0]), cur, s.acc_off,
                                     timing ? s.phase + 8 : nullptr);
                             decided = true;
-                            ++pair_done;
+                            if (tid == 0) ++s.jstat[2];
                         } else {
-                            ++pair_failed;
+                            if (tid == 0) ++s.jstat[3];
                         }
                     }
                     if (Pd > 0u) {
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                         st_release_u64(rflag, ((unsigned long long)wseq << 32) |
                                                   (pairs_on ? 0x80000000ull : 0ull) | nacc);
                     K += nacc;
-                    surv_total += Suse;
+                    if (tid == 0) s.jstat[1] += Suse;
                 } else {
                     __syncthreads();
                 }
@@ -796,7 +799,7 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     W = min(W * 2u, wmax_p);
                 W = min(W, wmax_p);
                 R0 = Rnext;
-                ++windows;
+                if (tid == 0) ++s.jstat[0];
                 if (lb > 0) {  // window t-1's accepts are window t+1's "t-2"
                     Word* tmp = acc_pp;
                     acc_pp = acc_p;
@@ -1059,8 +1062,10 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
                     if (pos < a.cache_words) cache[pos] = cur[i];
                 }
             }
-            ++windows;
-            surv_total += Suse;
+            if (tid == 0) {
+                ++s.jstat[0];
+                s.jstat[1] += Suse;
+            }
             if (S > 2u * job.target)
                 W = max(W / 2u, job.wmin);
             else if (S < job.target / 2u)
@@ -1092,11 +1097,11 @@ __global__ void __launch_bounds__(kBlock, 1) sweep_kernel(const __grid_constant_
         if (tid == 0 && lb == 0) {
             job.stats->codewords = K;
             job.stats->candidates = o.N;
-            job.stats->windows = windows;
-            job.stats->survivors = surv_total;
+            job.stats->windows = s.jstat[0];
+            job.stats->survivors = s.jstat[1];
             job.stats->strategy = job.strategy;
-            job.stats->pair_windows = pair_done;
-            job.stats->pair_fallbacks = pair_failed;
+            job.stats->pair_windows = s.jstat[2];
+            job.stats->pair_fallbacks = s.jstat[3];
         }
         if (timing)
             for (int k = 0; k < 12; ++k) job.stats->phase_cycles[k] = s.phase[k];
