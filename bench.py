@@ -272,6 +272,7 @@ def kernel_source_hash(files=None) -> str:
 
 
 GRID_SOURCES = ["gc_gridsweep.cu", "gc_block.cuh", "gc_device.cuh"]
+SWEEP_SOURCES = ["gc_sweep.cu", "gc_block.cuh", "gc_device.cuh"]   # sweep_kernel (captures)
 
 
 def recorded_traffic(profile: str, files=None):
