@@ -51,17 +51,22 @@
 
 namespace gc {
 
-constexpr int kGwSurvCap = 4096;        // survivors decided per window
+constexpr int kGwSurvCap = 8192;        // survivors decided per window
 constexpr int kGwChunk = 4096;          // candidates per CTA per window
-constexpr uint32_t kGwPairCap = 2048;   // pairs one CTA may list per window
+constexpr uint32_t kGwPairCap = 4096;   // pairs one CTA may list per window
 constexpr uint32_t kGwPairSmem = 16384; // pairs a CTA takes into shared memory
 constexpr uint32_t kGwPairGlobal = 8 * kGwPairSmem;  // pairs decided by rounds over L2
 constexpr int kGwMaxCtas = kBlock;      // one count per thread in the prefix scans
 constexpr int kGwProbeBatch = 14;       // high-bit probes a lookup issues at once
 static_assert(kGwSurvCap <= 65536, "pairs pack two entry indices in 16 bits each");
-static_assert(kGwSurvCap == 4 * kBlock, "the accept compaction gives a thread four entries");
+constexpr int kGwPerThread = kGwSurvCap / kBlock;   // window entries per thread
+static_assert(kGwSurvCap % (4 * kBlock) == 0, "threads take window entries four at a time");
+static_assert(kGwPerThread <= 8, "a thread's decisions fit one byte mask");
+static_assert(kGwPairSmem >= kResolveWords * kResolveBlock + kGwSurvCap,
+              "the conflict-matrix fallback keeps its accepts' offsets after its matrix");
+constexpr uint32_t kGwPairTarget = 8000;   // pairs a window is sized for
 static_assert(kGwPairCap <= kGwPairSmem, "a CTA's own pairs are staged in the pair area");
-static_assert(kGwPairCap <= 2 * kBlock, "a thread publishes at most two of its CTA's pairs");
+static_assert(kGwPairCap == 4 * kBlock, "a thread publishes at most four of its CTA's pairs");
 
 struct GwArgs {
     Order ord;
@@ -90,8 +95,12 @@ struct GwArgs {
     uint32_t pair_smem;       // pairs decided from shared memory (<= kGwPairSmem)
     uint32_t early;           // 1 (with probe): window t-1's balls marked in phase A of
                               // window t, rows probed in phase B instead of tested
+    uint32_t* cnt;            // d = 3 (with early): byte v counts the current window's
+                              // survivors within distance 1 of vector v (indexed like
+                              // the bitmap: bit-reversed for grevlex); null: unused
 };
 
+struct __align__(16) GwSmem;
 struct __align__(16) GwSmem {
     uint32_t C[kMaxN + 1][kMaxN + 1];
     uint32_t lowball[8][32];  // lowball[r][c]: bits y < 32 with popc(y ^ c) <= r
@@ -100,9 +109,7 @@ struct __align__(16) GwSmem {
     __align__(16) uint32_t wx[kGwSurvCap];      // own chunk (A), the window (B)
     __align__(16) uint32_t woff[kGwSurvCap];
     __align__(16) uint32_t ax[kGwSurvCap];      // the previous window's accepts
-    __align__(16) uint32_t ax_off[kGwSurvCap];  // and their ranks (n <= 32)
-    __align__(16) uint32_t acc[kGwSurvCap];     // block_resolve's output; B: own rows
-    __align__(16) uint32_t acc_off[kGwSurvCap];
+    __align__(16) uint32_t rx[kGwSurvCap];      // B: this CTA's rows, contiguous
     uint8_t state[kGwSurvCap];                  // 0 undecided, 1 accepted, 2 rejected
     uint8_t flags[2 * kGwSurvCap];              // row kills (B); killed / blocked (rounds)
     BlockScratch bs;
@@ -115,6 +122,8 @@ struct __align__(16) GwSmem {
         uint32_t M[kResolveWords][kResolveBlock];
     } u;
 };
+
+static_assert(sizeof(GwSmem) <= 232448, "one CTA per SM: at most 227 KiB of shared memory");
 
 // CTA-wide grid barrier: one arrival per CTA on a counter that only grows;
 // the barrier of epoch e is passed once it reaches (e + 1) * arrivals.  The
@@ -151,10 +160,9 @@ __device__ bool gw_sync(GwSmem& s, const GwArgs& a, uint32_t& epoch) {
 // and 0 for the rest; pairs[0..P) hold (k << 16) | i for conflicting pairs
 // k < i.  Each round decides every undecided entry whose earlier neighbours
 // are all decided (the first undecided entry always is, so the rounds end);
-// then the accepts x[i] and their ranks R0 + off[i] are appended in order to
-// ax/ax_off.  Returns how many; counts rounds in *rounds.
-__device__ uint32_t gw_pair_rounds(GwSmem& s, uint32_t n, uint32_t P, uint64_t R0,
-                                   uint64_t* rounds) {
+// then the accepts x[i] are appended in order to ax.  Returns how many;
+// counts rounds in *rounds.
+__device__ uint32_t gw_pair_rounds(GwSmem& s, uint32_t n, uint32_t P, uint64_t* rounds) {
     uint8_t* killed = s.flags;
     uint8_t* blocked = s.flags + kGwSurvCap;
     const int lane = lane_id();
@@ -195,8 +203,7 @@ __device__ uint32_t gw_pair_rounds(GwSmem& s, uint32_t n, uint32_t P, uint64_t R
     for (uint32_t t0 = 0; t0 < n; t0 += kBlock) {
         const uint32_t i = t0 + threadIdx.x;
         const bool keep = i < n && s.state[i] == 1;
-        nacc = block_append(s.bs, keep, keep ? s.wx[i] : 0u,
-                            keep ? (uint32_t)(R0 + s.woff[i]) : 0u, s.ax, s.ax_off, nacc);
+        nacc = block_append(s.bs, keep, keep ? s.wx[i] : 0u, 0u, s.ax, (uint32_t*)nullptr, nacc);
     }
     return nacc;
 }
@@ -339,6 +346,12 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         const uint64_t per = (words + G - 1) / G;
         const uint64_t w0 = min((uint64_t)lb * per, words), w1 = min(w0 + per, words);
         for (uint64_t w = w0 + tid; w < w1; w += kBlock) a.bitmap[w] = 0u;
+        if (a.cnt) {
+            const uint64_t cw = (1ull << n) / 4 > 0 ? ((1ull << n) + 3) / 4 : 1;
+            const uint64_t cper = (cw + G - 1) / G;
+            const uint64_t c0 = min((uint64_t)lb * cper, cw), c1 = min(c0 + cper, cw);
+            for (uint64_t w = c0 + tid; w < c1; w += kBlock) a.cnt[w] = 0u;
+        }
     }
     uint32_t epoch = 0;
     bool ok = gw_sync(s, a, epoch);
@@ -346,7 +359,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
     // bit k: the window entry tid + k * kBlock this thread gathers is one of
     // this CTA's rows (entries lb + r * G)
     uint32_t own = 0;
-    for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k) {
+    for (uint32_t k = 0; k < (uint32_t)kGwPerThread; ++k) {
         const uint32_t e = tid + k * kBlock;
         if (e >= lb && (e - lb) % G == 0u) own |= 1u << k;
     }
@@ -418,12 +431,29 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         }
     };
 
+    // d = 3: survivors' radius-1 balls in the byte counters, +1 (add) or -1.
+    // Item q of m * (n + 1) is vector ys[q % m] with bit q / m flipped (bit n:
+    // none), so consecutive lanes touch neighbouring survivors' balls.
+    auto count_balls = [&](const uint32_t* ys, bool global_src, uint32_t m, bool add) {
+        const uint32_t items = m * (uint32_t)(n + 1);
+        for (uint32_t q = tid; q < items; q += kBlock) {
+            const uint32_t j = q / m, i = q - j * m;
+            uint32_t y = global_src ? ld_cg(ys + i) : ys[i];
+            if (a.reversed) y = reverse_n(y, n);   // indexed like the bitmap
+            const uint32_t v = (int)j < n ? y ^ (1u << j) : y;
+            const uint32_t one = 1u << (8u * (v & 3u));
+            if (add) atomicAdd(a.cnt + (v >> 2), one);
+            else atomicSub(a.cnt + (v >> 2), one);
+        }
+    };
+    uint32_t na_prev = 0;   // this CTA's survivors in the previous window
+
     uint64_t R0 = 0, K = 0, Kprev = 0;
     uint32_t W = a.wmin, nprev = 0;
     uint64_t my_tests = 0, dense = 0, windows = 0, surv_total = 0;
     uint64_t pair_windows = 0, fallbacks = 0, rounds_total = 0;
-    // ax/ax_off[0..nprev): the accepts of the previous window, in every CTA;
-    // this CTA's share of them goes to the output
+    // ax[0..nprev): the accepts of the previous window, in every CTA; this
+    // CTA's share of them goes to the output
     auto emit_prev = [&]() {
         const uint32_t per = (nprev + G - 1) / G;
         const uint32_t i0 = min(lb * per, nprev), i1 = min(i0 + per, nprev);
@@ -431,9 +461,10 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             const uint64_t pos = Kprev + i;
             if (pos < a.cap) a.out[pos] = s.ax[i];
         }
-        if (lb == 0 && !o.filter)
-            for (uint32_t i = tid; i < nprev; i += kBlock) dense += o.N - 1 - s.ax_off[i];
     };
+    // dense-equivalent tests (statistics, CTA 0): an accept of rank R is
+    // compared with every later candidate
+    const bool count_dense = lb == 0 && !o.filter;
     uint32_t t = 0;
     for (; ok && R0 < o.N; ++t) {
         const int p = t & 1;
@@ -486,6 +517,13 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             }
             uint32_t* sx = a.seg_x + ((size_t)p * G + lb) * kGwChunk;
             uint32_t* so = a.seg_off + ((size_t)p * G + lb) * kGwChunk;
+            if (a.cnt) {
+                // the previous window's survivors out of the counters, this
+                // window's in (complete at this phase's barrier)
+                count_balls(a.seg_x + ((size_t)(p ^ 1) * G + lb) * kGwChunk, true, na_prev, false);
+                count_balls(s.wx, false, na, true);
+                na_prev = na;
+            }
             for (uint32_t i = tid; i < na; i += kBlock) {
                 sx[i] = s.wx[i];
                 so[i] = s.woff[i];
@@ -512,12 +550,14 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         const uint32_t Suse = min(S, (uint32_t)kGwSurvCap);
         if (tid == 0) s.npairs = 0;
         // entry e of the window sits in the segment of the last CTA g with
-        // pref[g] <= e (empty segments share their successor's prefix)
-        {
-            uint32_t at[kGwSurvCap / kBlock];  // < 2 * grid * kGwChunk
+        // pref[g] <= e (empty segments share their successor's prefix); a
+        // thread gathers its entries four at a time
+#pragma unroll 1
+        for (uint32_t h = 0; h < (uint32_t)kGwPerThread; h += 4) {
+            uint32_t at[4];  // < 2 * grid * kGwChunk
 #pragma unroll
-            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k) {
-                const uint32_t e = tid + k * kBlock;
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t e = tid + (h + k) * kBlock;
                 uint32_t lo = 0, hi = G;
                 while (hi - lo > 1u) {
                     const uint32_t mid = (lo + hi) >> 1;
@@ -526,21 +566,21 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 }
                 at[k] = ((uint32_t)p * G + lo) * (uint32_t)kGwChunk + (e - s.pref[lo]);
             }
-            uint32_t vx[kGwSurvCap / kBlock], vo[kGwSurvCap / kBlock];
+            uint32_t vx[4], vo[4];
 #pragma unroll
-            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k)
-                if (tid + k * kBlock < Suse) {
+            for (uint32_t k = 0; k < 4; ++k)
+                if (tid + (h + k) * kBlock < Suse) {
                     vx[k] = ld_cg(a.seg_x + at[k]);
                     vo[k] = ld_cg(a.seg_off + at[k]);
                 }
 #pragma unroll
-            for (uint32_t k = 0; k < kGwSurvCap / kBlock; ++k) {
-                const uint32_t e = tid + k * kBlock;
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t e = tid + (h + k) * kBlock;
                 if (e < Suse) {
                     s.wx[e] = vx[k];
                     s.woff[e] = vo[k];
-                    // this CTA's rows also go to acc, contiguous
-                    if ((own >> k) & 1u) s.acc[(e - lb) / G] = vx[k];
+                    // this CTA's rows also go to rx, contiguous
+                    if ((own >> (h + k)) & 1u) s.rx[(e - lb) / G] = vx[k];
                 }
             }
         }
@@ -559,16 +599,31 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 // one high bit j away, lane 31 the row's own word.
                 const int nh = n > 5 ? n - 5 : 0;
                 for (uint32_t r = warp_id(); r < rows; r += kWarps) {
-                    const uint32_t x = s.acc[r];
+                    const uint32_t x = s.rx[r];
                     const uint32_t key = a.reversed ? reverse_n(x, n) : x;
                     const uint32_t w0 = key >> 5, b = key & 31u;
                     bool hit = false;
                     if (lane < nh) hit = ((ld_cg(a.bitmap + (w0 ^ (1u << lane))) >> b) & 1u) != 0u;
                     else if (lane == 31) hit = (ld_cg(a.bitmap + w0) & s.lowball[1][b]) != 0u;
                     hit = __any_sync(kFull, hit);
-                    if (lane == 0) s.flags[r] = hit ? 1 : 0;
+                    if (a.cnt && !hit) {
+                        // d = 3: the counts over x's radius-1 ball add up
+                        // to n + 1 (x's own ball) plus two for each other
+                        // survivor of the window within distance 2 of x
+                        uint32_t c = 0;
+                        if (lane < n) {
+                            const uint32_t v = key ^ (1u << lane);
+                            c = (ld_cg(a.cnt + (v >> 2)) >> (8u * (v & 3u))) & 0xffu;
+                        }
+                        if (lane == 0) c += (ld_cg(a.cnt + (key >> 2)) >> (8u * (key & 3u))) & 0xffu;
+                        c = __reduce_add_sync(kFull, c);
+                        if (lane == 0) s.flags[r] = c > (uint32_t)(n + 1) ? 2 : 0;
+                    } else if (lane == 0) {
+                        s.flags[r] = hit ? 1 : 0;
+                    }
                 }
                 mark_begin(0);
+                if (a.cnt) __syncthreads();   // the tests below read the flags
                 mark_phase(3);
             } else {
                 // window t-1's marks, spread over the tests below: a slice
@@ -576,7 +631,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 mark_begin(nprev);
             }
             const uint32_t mslice = (mark_left() + 7u) / 8u;
-            const uint32_t* rx = s.acc;   // this CTA's rows, contiguous
+            const uint32_t* rx = s.rx;   // this CTA's rows, contiguous
             // the previous window's accepts against every row
             for (uint32_t c = tid; c < (a.early ? 0u : nprev); c += kBlock) {
                 mark_some(mslice);
@@ -601,7 +656,33 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 const uint32_t e = atomicAdd(&s.npairs, 1u);
                 if (e < kGwPairCap) s.u.pairs[e] = (k << 16) | i;
             };
-            if (a.early) {
+            if (a.cnt) {
+                // d = 3: only the rows that meet another survivor of the
+                // window, a warp per row, against every earlier entry
+                for (uint32_t r = warp_id(); r < rows; r += kWarps) {
+                    if (s.flags[r] != 2) continue;
+                    const uint32_t i = lb + r * G, x = rx[r];
+                    for (uint32_t k0 = 0; k0 < i; k0 += 128u) {
+                        const uint32_t k = k0 + 4u * (uint32_t)lane;
+                        const uint4 q = *reinterpret_cast<const uint4*>(s.wx + k);
+                        int m0 = popc(q.x ^ x), m1 = popc(q.y ^ x);
+                        int m2 = popc(q.z ^ x), m3 = popc(q.w ^ x);
+                        if (k0 + 128u > i) {   // entries from i on
+                            if (k >= i) m0 = 32;
+                            if (k + 1u >= i) m1 = 32;
+                            if (k + 2u >= i) m2 = 32;
+                            if (k + 3u >= i) m3 = 32;
+                        }
+                        if (min(min(m0, m1), min(m2, m3)) < d) {
+                            if (m0 < d) pair(k, i);
+                            if (m1 < d) pair(k + 1u, i);
+                            if (m2 < d) pair(k + 2u, i);
+                            if (m3 < d) pair(k + 3u, i);
+                        }
+                    }
+                    if (lane == 0) my_tests += i;
+                }
+            } else if (a.early) {
                 // the window's entries against the later rows: pairs (k, i),
                 // k < i.  Row r (entry i_r = lb + r * G) meets the i_r entries
                 // before it; the (row, entry) triangle, flattened row by row
@@ -651,9 +732,9 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 // the window's entries against the later rows, a thread per
                 // entry (column) with window t-1's marks between them.  Entry
                 // k meets the rows after it, so a thread takes columns from
-                // both ends of each half of the window (tid, 2047 - tid,
-                // 2048 + tid, 4095 - tid) and every thread has about the same
-                // tests.
+                // both ends of each pair of kBlock-column blocks (tid, 2047 -
+                // tid, 2048 + tid, 4095 - tid, ...) and every thread has about
+                // the same tests.
 #pragma unroll 1
                 for (uint32_t m = 0; m < (uint32_t)kGwSurvCap / kBlock; ++m) {
                     const uint32_t k = (m & 1u) ? kBlock * (m + 1u) - 1u - tid : kBlock * m + tid;
@@ -684,30 +765,29 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             __syncthreads();
             mark_phase(6);
             // publish: the kills, and the pairs whose later entry survived
-            for (uint32_t r = tid; r < rows; r += kBlock) a.killbuf[lb + r * G] = s.flags[r];
+            for (uint32_t r = tid; r < rows; r += kBlock) a.killbuf[lb + r * G] = s.flags[r] == 1 ? 1 : 0;
             const uint32_t np = s.npairs;
             uint32_t kept = 0;
             if (np <= kGwPairCap) {
                 // the pairs whose later entry survived go to the window's
                 // list, at an offset reserved on its counter (the pairs'
                 // order does not matter, their count does)
-                uint32_t pr0 = 0, pr1 = 0;
-                bool k0 = false, k1 = false;
-                if ((uint32_t)tid < np) {
-                    pr0 = s.u.pairs[tid];
-                    k0 = s.flags[((pr0 & 0xffffu) - lb) / G] == 0;
+                uint32_t pr[4];
+                uint32_t km = 0;   // bit u: pair tid + u * kBlock is kept
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t e = tid + u * kBlock;
+                    pr[u] = e < np ? s.u.pairs[e] : 0u;
+                    if (e < np && s.flags[((pr[u] & 0xffffu) - lb) / G] != 1) km |= 1u << u;
                 }
-                if ((uint32_t)tid + kBlock < np) {
-                    pr1 = s.u.pairs[tid + kBlock];
-                    k1 = s.flags[((pr1 & 0xffffu) - lb) / G] == 0;
-                }
-                uint32_t pos = block_exclusive_scan(s.bs, (uint32_t)k0 + (uint32_t)k1, &kept);
+                uint32_t pos = block_exclusive_scan(s.bs, (uint32_t)__popc(km), &kept);
                 if (tid == 0 && kept) s.bs.bcast64 = atomicAdd(a.ctrl + 2 + p, kept);
                 __syncthreads();
-                if (kept) {
+                if (km) {
                     const uint32_t base = (uint32_t)s.bs.bcast64;
-                    if (k0) a.pairbuf[base + pos++] = pr0;
-                    if (k1) a.pairbuf[base + pos] = pr1;
+#pragma unroll
+                    for (uint32_t u = 0; u < 4; ++u)
+                        if ((km >> u) & 1u) a.pairbuf[base + pos++] = pr[u];
                 }
             }
             if (tid == 0) a.pslot[(size_t)p * G + lb] = np <= kGwPairCap ? kept : kGwPairCap + 1u;
@@ -719,19 +799,21 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
 
         // ---- every CTA decides the window from the same data
         const uint32_t v = (uint32_t)tid < G ? ld_cg(a.pslot + (size_t)p * G + tid) : 0u;
-        {
-            // four entries per thread: one 4-byte load of their kill bytes
-            const uint32_t e0 = 4u * tid;
+        // kGwPerThread consecutive entries per thread, their kill bytes read
+        // four at a time
+        const uint32_t e0 = (uint32_t)kGwPerThread * tid;
+#pragma unroll
+        for (uint32_t q = 0; q < (uint32_t)kGwPerThread; q += 4) {
             uint32_t kw = 0;
-            if (e0 + 4 <= Suse) {
-                kw = __ldcg(reinterpret_cast<const unsigned*>(a.killbuf + e0));
+            if (e0 + q + 4 <= Suse) {
+                kw = __ldcg(reinterpret_cast<const unsigned*>(a.killbuf + e0 + q));
             } else {
-                for (uint32_t k = 0; e0 + k < Suse; ++k)
-                    kw |= (uint32_t)__ldcg(a.killbuf + e0 + k) << (8 * k);
+                for (uint32_t k = 0; e0 + q + k < Suse && k < 4; ++k)
+                    kw |= (uint32_t)__ldcg(a.killbuf + e0 + q + k) << (8 * k);
             }
 #pragma unroll
             for (uint32_t k = 0; k < 4; ++k)
-                if (e0 + k < Suse) s.state[e0 + k] = ((kw >> (8 * k)) & 0xffu) ? 2 : 0;
+                if (e0 + q + k < Suse) s.state[e0 + q + k] = ((kw >> (8 * k)) & 0xffu) ? 2 : 0;
         }
         const uint32_t P = ld_cg(a.ctrl + 2 + p);
         // a CTA's list overflowed, or the window's is too long for rounds
@@ -742,19 +824,19 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         if (!over && P == 0u) {
             // no conflict inside the window: the entries no previous accept
             // rejected are the accepts
-            const uint32_t e0 = 4u * tid;
             uint32_t keepm = 0;
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k)
+            for (uint32_t k = 0; k < (uint32_t)kGwPerThread; ++k)
                 if (e0 + k < Suse && s.state[e0 + k] == 0) keepm |= 1u << k;
             uint32_t pos = block_exclusive_scan(s.bs, __popc(keepm), &nacc);
+            uint32_t osum = 0;   // offsets of this thread's accepts (< 8 * 2^20)
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k)
+            for (uint32_t k = 0; k < (uint32_t)kGwPerThread; ++k)
                 if ((keepm >> k) & 1u) {
-                    s.ax[pos] = s.wx[e0 + k];
-                    s.ax_off[pos] = (uint32_t)(R0 + s.woff[e0 + k]);
-                    ++pos;
+                    s.ax[pos++] = s.wx[e0 + k];
+                    osum += s.woff[e0 + k];
                 }
+            if (count_dense) dense += (uint64_t)__popc(keepm) * (o.N - 1 - R0) - osum;
             __syncthreads();
         } else if (!over) {
             uint32_t Ps = P;
@@ -765,22 +847,25 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
                 // too many for shared memory: the first rounds from L2
                 Ps = gw_pair_rounds_global(s, a.pairbuf, P, Suse, a.pair_smem, &rounds_total);
             }
-            nacc = gw_pair_rounds(s, Suse, Ps, R0, &rounds_total);
+            nacc = gw_pair_rounds(s, Suse, Ps, &rounds_total);
+            if (count_dense)
+                for (uint32_t i = tid; i < Suse; i += kBlock)
+                    if (s.state[i] == 1) dense += o.N - 1 - R0 - s.woff[i];
             ++pair_windows;
             mark_phase(9);
         } else {
             // drop the entries a previous accept rejects, then the conflict
-            // matrices
+            // matrices; the accepts go straight to ax, their offsets after the
+            // matrices in the pair area
             __syncthreads();
             const uint32_t m = block_compact(s.bs, s.wx, s.woff, s.state, Suse);
             uint64_t rt = 0;
-            nacc = block_resolve<false>(s.bs, s.wx, s.woff, s.flags, m, d, s.acc, s.acc_off,
+            uint32_t* fb_off = &s.u.pairs[kResolveWords * kResolveBlock];
+            nacc = block_resolve<false>(s.bs, s.wx, s.woff, s.flags, m, d, s.ax, fb_off,
                                         s.u.M, rt, nullptr, 384u);
             if (lb == 0) my_tests += rt;
-            for (uint32_t i = tid; i < nacc; i += kBlock) {
-                s.ax[i] = s.acc[i];
-                s.ax_off[i] = (uint32_t)(R0 + s.acc_off[i]);
-            }
+            if (count_dense)
+                for (uint32_t i = tid; i < nacc; i += kBlock) dense += o.N - 1 - R0 - fb_off[i];
             __syncthreads();
             ++fallbacks;
             mark_phase(10);
@@ -792,11 +877,19 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         ++windows;
         surv_total += Suse;
         // the next window aims at `target` survivors at the density this one
-        // had (at most twice as long)
+        // had (at most twice as long), fewer where the survivors conflict
+        // densely: about kGwPairTarget pairs at this window's pair density
         {
+            uint64_t tgt = a.target;
+            const uint32_t Peff = over ? max(P, 4u * kGwPairTarget) : P;
+            if (Peff > kGwPairTarget && Suse > 0) {
+                const float f = sqrtf((float)kGwPairTarget / (float)Peff);
+                const uint64_t t2 = (uint64_t)((float)Suse * f);
+                if (t2 < tgt) tgt = t2 > 256u ? t2 : 256u;
+            }
             const uint64_t used = Rnext - R0;
             const uint64_t grow = 2ull * (uint64_t)W;
-            uint64_t want = Suse ? used * (uint64_t)a.target / Suse : grow;
+            uint64_t want = Suse ? used * tgt / Suse : grow;
             if (want > grow) want = grow;
             if (want < (uint64_t)a.wmin) want = a.wmin;
             if (want > (uint64_t)a.wmax) want = a.wmax;
@@ -842,6 +935,21 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
 // ------------------------------------------------------------------ host side
 static size_t gw_align(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// The launch's forms, from the problem and the switches (the layout and the
+// launch must agree): early marks for every d >= 2 unless GC_GRID_EARLY=0;
+// with them, for d = 3, byte counters of the window's survivors so that only
+// rows that meet another survivor are tested (GC_GRID_CONF=0: all rows).
+static bool gw_early(const HostProblem& p) {
+    if (p.d < 2) return false;
+    const char* e = std::getenv("GC_GRID_EARLY");
+    return !e || std::atoi(e) != 0;
+}
+static bool gw_counters(const HostProblem& p) {
+    if (p.d != 3 || !gw_early(p)) return false;
+    const char* e = std::getenv("GC_GRID_CONF");
+    return !e || std::atoi(e) != 0;
+}
+
 bool grid_sweep_layout(const HostProblem& p, const gc_plan_t& plan, GridLayout* L,
                        std::string* why) {
     int dev = 0, sms = 0, optin = 0;
@@ -880,6 +988,11 @@ bool grid_sweep_layout(const HostProblem& p, const gc_plan_t& plan, GridLayout* 
     L->off_kill = off;    off += gw_align(kGwSurvCap);
     L->off_hball = off;   off += gw_align(4 * high_ball_len(p.n, p.d));
     L->off_bitmap = off;  off += gw_align(((1ull << p.n) + 31) / 32 * 4);
+    L->off_cnt = 0;
+    if (gw_counters(p)) {
+        L->off_cnt = off;
+        off += gw_align(std::max<uint64_t>(4, 1ull << p.n));
+    }
     L->total = off;
     const uint64_t wcap = (uint64_t)grid * kGwChunk;
     L->wmax = (uint32_t)std::min<uint64_t>(plan.window_max ? plan.window_max : wcap, wcap);
@@ -916,8 +1029,7 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     // d >= 4, d-1 below, unless GC_GRID_PROBE says otherwise)
     uint32_t probe = p.d >= 4 ? 1u : 0u;
     if (const char* e = std::getenv("GC_GRID_PROBE")) probe = std::atoi(e) != 0 && p.d >= 2 ? 1u : 0u;
-    uint32_t early = p.d >= 2 ? 1u : 0u;
-    if (const char* e = std::getenv("GC_GRID_EARLY")) early = std::atoi(e) != 0 && p.d >= 2 ? 1u : 0u;
+    const uint32_t early = gw_early(p) ? 1u : 0u;
     if (early) probe = 1u;
     const int rad = p.d - 1 - (int)probe;
     const uint32_t hl = (uint32_t)high_ball_len(p.n, rad + 1);
@@ -956,6 +1068,7 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     a.reversed = p.ord == GC_ORDER_GREVLEX ? 1u : 0u;
     a.probe = probe;
     a.early = early;
+    a.cnt = L.off_cnt ? reinterpret_cast<uint32_t*>(ws + L.off_cnt) : nullptr;
     // GC_GRID_PAIR_SMEM (tests): decide windows of more pairs through the
     // rounds over the global list
     a.pair_smem = kGwPairSmem;

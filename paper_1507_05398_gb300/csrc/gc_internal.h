@@ -38,10 +38,11 @@ constexpr uint32_t kTargetBitmap = 1024;
 constexpr uint64_t kLargeSweep = 1ull << 28;
 // GC_TARGET_BITMAP overrides the bitmap target of sweeps below kLargeSweep
 // candidates (measurements).
-// The grid bitmap sweep decides at most 4096 survivors per window and cuts
+// The grid bitmap sweep decides at most 8192 survivors per window and cuts
 // the window after them; it aims a little above that, so that windows end at
-// the cut and little of the generated window is thrown away.
-constexpr uint32_t kTargetGrid = 4400;
+// the cut and little of the generated window is thrown away (windows whose
+// survivors conflict densely aim lower, by their pair density).
+constexpr uint32_t kTargetGrid = 8800;
 inline uint32_t default_target(int strategy, const HostProblem& p) {
     if (strategy == GC_STRATEGY_BITMAP_GRID) return kTargetGrid;
     if (strategy != GC_STRATEGY_BITMAP) return kTargetDistance;
@@ -168,6 +169,7 @@ struct GridLayout {
     size_t smem_bytes = 0;
     size_t off_ctrl = 0, off_slot = 0, off_pslot = 0, off_segx = 0, off_segoff = 0;
     size_t off_pairs = 0, off_kill = 0, off_hball = 0, off_bitmap = 0;
+    size_t off_cnt = 0;        // d = 3: 2^n byte counters (0: none)
     size_t total = 0;
     uint32_t wmin = 0, wmax = 0, target = 0;
 };

@@ -175,20 +175,24 @@ def test_grid_strategy_mid_and_weighted(o, n, d, w):
 
 
 @pytest.mark.parametrize("env", [{"GC_GRID_PROBE": "0"}, {"GC_GRID_PROBE": "1"},
-                                 {"GC_GRID_EARLY": "1"}, {"GC_GRID_EARLY": "0"}])
+                                 {"GC_GRID_EARLY": "1"}, {"GC_GRID_EARLY": "0"},
+                                 {"GC_GRID_CONF": "0"}])
 def test_grid_radius_split_both_ways(env, monkeypatch):
     """The grid sweep either marks radius-(d-1) balls and looks up one bit,
     or marks radius-(d-2) balls and probes the candidate's radius-1
     neighbourhood; with early marks, window t-1's balls go into the bitmap
     before window t's rows are probed against it instead of tested against
-    window t-1's accepts.  GC_GRID_PROBE / GC_GRID_EARLY force each form.
-    All give the oracle's code, in every order, with and without a weight."""
+    window t-1's accepts; for d = 3, byte counters of the window's survivors
+    let only the rows that meet another survivor run the pair tests.
+    GC_GRID_PROBE / GC_GRID_EARLY / GC_GRID_CONF force each form.  All give
+    the oracle's code, in every order, with and without a weight."""
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     for n, d, o, w in [(18, 3, "lex", -1), (19, 4, "gray", -1), (20, 4, "grevlex", -1),
                        (20, 5, "grlex", -1), (21, 6, "lex", -1), (18, 4, "grevlex", 7),
                        (20, 4, "gray", 9), (9, 4, "lex", -1), (5, 3, "grlex", -1),
-                       (20, 3, "grevlex", -1), (19, 3, "gray", 6), (4, 2, "lex", -1)]:
+                       (20, 3, "grevlex", -1), (19, 3, "gray", 6), (4, 2, "lex", -1),
+                       (21, 3, "lex", -1), (3, 3, "gray", -1), (2, 3, "lex", -1)]:
         got, st = gpu_code(n, d, o, w, "grid")
         assert got.tolist() == oracle.greedy_ball(n, d, o, w).tolist(), (env, n, d, o, w)
 
