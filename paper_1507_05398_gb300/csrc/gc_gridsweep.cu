@@ -64,7 +64,7 @@ static_assert(kGwSurvCap % (4 * kBlock) == 0, "threads take window entries four 
 static_assert(kGwPerThread <= 8, "a thread's decisions fit one byte mask");
 static_assert(kGwPairSmem >= kResolveWords * kResolveBlock + kGwSurvCap,
               "the conflict-matrix fallback keeps its accepts' offsets after its matrix");
-constexpr uint32_t kGwPairTarget = 8000;   // pairs a window is sized for
+constexpr uint32_t kGwPairTargetDefault = 16000;  // pairs a window is sized for
 static_assert(kGwPairCap <= kGwPairSmem, "a CTA's own pairs are staged in the pair area");
 static_assert(kGwPairCap == 4 * kBlock, "a thread publishes at most four of its CTA's pairs");
 
@@ -93,6 +93,7 @@ struct GwArgs {
     uint32_t reversed;        // 1: the bitmap is indexed by the bit-reversed vector
     uint32_t probe;           // 1: radius-(d-2) balls marked, lookups probe radius 1
     uint32_t pair_smem;       // pairs decided from shared memory (<= kGwPairSmem)
+    uint32_t pair_target;     // pairs the next window is sized for
     uint32_t early;           // 1 (with probe): window t-1's balls marked in phase A of
                               // window t, rows probed in phase B instead of tested
     uint32_t* cnt;            // d = 3 (with early): byte v counts the current window's
@@ -881,9 +882,9 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         // densely: about kGwPairTarget pairs at this window's pair density
         {
             uint64_t tgt = a.target;
-            const uint32_t Peff = over ? max(P, 4u * kGwPairTarget) : P;
-            if (Peff > kGwPairTarget && Suse > 0) {
-                const float f = sqrtf((float)kGwPairTarget / (float)Peff);
+            const uint32_t Peff = over ? max(P, 4u * a.pair_target) : P;
+            if (Peff > a.pair_target && Suse > 0) {
+                const float f = sqrtf((float)a.pair_target / (float)Peff);
                 const uint64_t t2 = (uint64_t)((float)Suse * f);
                 if (t2 < tgt) tgt = t2 > 256u ? t2 : 256u;
             }
@@ -1072,6 +1073,9 @@ int launch_grid_sweep(const HostProblem& p, const GridLayout& L, uint32_t* d_out
     // GC_GRID_PAIR_SMEM (tests): decide windows of more pairs through the
     // rounds over the global list
     a.pair_smem = kGwPairSmem;
+    a.pair_target = kGwPairTargetDefault;
+    if (const char* e = std::getenv("GC_GRID_PAIR_TARGET"))
+        a.pair_target = (uint32_t)std::max(64, std::atoi(e));
     if (const char* e = std::getenv("GC_GRID_PAIR_SMEM"))
         a.pair_smem = (uint32_t)std::max(1, std::min((int)kGwPairSmem, std::atoi(e)));
     void* args[] = {&a};
