@@ -23,15 +23,27 @@
 //     window is cut after them).  It probes its rows (entries i = CTA index
 //     mod grid) against the bitmap, now complete up to window t-1 -- a hit
 //     rejects the entry -- and tests them against every earlier entry of the
-//     window, listing the conflicting pairs (Hamming distance < d).  A
-//     thread takes columns (entries) and tests each against all the CTA's
-//     rows, which sit contiguous in shared memory, four to a 16-byte load.
+//     window, listing the conflicting pairs (Hamming distance < d).  The
+//     (row, earlier entry) triangle is cut into one equal span per warp,
+//     whose lanes sweep consecutive entries, four to a 16-byte load, against
+//     the row word the warp holds.  For d = 3 a 2^n-byte array counts, for
+//     each vector, the window's survivors within distance 1 of it (each CTA
+//     adds its survivors' radius-1 balls in phase A and takes its previous
+//     window's out); the counts over a row's own radius-1 ball add up to
+//     n + 1 plus two for every other survivor within distance 2, so only the
+//     rows above n + 1 run the tests -- in most windows, none.
+//     Each CTA publishes its rows' kills and its pairs, the pairs into one
+//     list for the window at offsets reserved on a counter.
 // Then every CTA, from the same data, decides the window exactly as the
 // serial loop would: with no pair, the entries no accept rejected are the
 // accepts; otherwise rounds over the pair list (an entry is rejected once an
 // earlier neighbour is accepted and accepted once every earlier neighbour is
-// rejected); when the list is too long, the conflict matrices of
-// block_resolve.  Every CTA keeps the accepts for the next window.
+// rejected), from shared memory, or first over the list in L2 while it is
+// too long for shared memory; when it is longer still, the conflict
+// matrices of block_resolve.  Every CTA keeps the accepts for the next
+// window.  The next window aims at kGwSurvCap survivors at the density this
+// one had, fewer where its survivors conflict densely (sized for a set
+// number of pairs at this window's pair density).
 // A second form (GC_GRID_EARLY=0) marks window t-1's balls between the row
 // tests of phase B and tests the rows against window t-1's accepts instead
 // of probing them; with GC_GRID_PROBE=0 as well, it marks radius-(d-1) balls
@@ -61,7 +73,7 @@ constexpr int kGwProbeBatch = 14;       // high-bit probes a lookup issues at on
 static_assert(kGwSurvCap <= 65536, "pairs pack two entry indices in 16 bits each");
 constexpr int kGwPerThread = kGwSurvCap / kBlock;   // window entries per thread
 static_assert(kGwSurvCap % (4 * kBlock) == 0, "threads take window entries four at a time");
-static_assert(kGwPerThread <= 8, "a thread's decisions fit one byte mask");
+static_assert(kGwPerThread == 8, "a thread decides eight consecutive entries");
 static_assert(kGwPairSmem >= kResolveWords * kResolveBlock + kGwSurvCap,
               "the conflict-matrix fallback keeps its accepts' offsets after its matrix");
 constexpr uint32_t kGwPairTargetDefault = 16000;  // pairs a window is sized for
@@ -800,21 +812,33 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
 
         // ---- every CTA decides the window from the same data
         const uint32_t v = (uint32_t)tid < G ? ld_cg(a.pslot + (size_t)p * G + tid) : 0u;
-        // kGwPerThread consecutive entries per thread, their kill bytes read
-        // four at a time
+        // kGwPerThread (8) consecutive entries per thread: their kill bytes in
+        // two 4-byte loads, their states in one 8-byte store (consecutive
+        // threads 8 entries apart would otherwise meet in the same banks)
         const uint32_t e0 = (uint32_t)kGwPerThread * tid;
+        uint32_t keepm = 0;   // bit k: entry e0 + k exists and no accept rejected it
+        {
+            uint32_t kw[2];
 #pragma unroll
-        for (uint32_t q = 0; q < (uint32_t)kGwPerThread; q += 4) {
-            uint32_t kw = 0;
-            if (e0 + q + 4 <= Suse) {
-                kw = __ldcg(reinterpret_cast<const unsigned*>(a.killbuf + e0 + q));
-            } else {
-                for (uint32_t k = 0; e0 + q + k < Suse && k < 4; ++k)
-                    kw |= (uint32_t)__ldcg(a.killbuf + e0 + q + k) << (8 * k);
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t q = 4u * h;
+                kw[h] = 0;
+                if (e0 + q + 4 <= Suse) {
+                    kw[h] = __ldcg(reinterpret_cast<const unsigned*>(a.killbuf + e0 + q));
+                } else {
+                    for (uint32_t k = 0; e0 + q + k < Suse && k < 4; ++k)
+                        kw[h] |= (uint32_t)__ldcg(a.killbuf + e0 + q + k) << (8 * k);
+                }
             }
+            uint32_t st[2] = {0u, 0u};
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k)
-                if (e0 + q + k < Suse) s.state[e0 + q + k] = ((kw >> (8 * k)) & 0xffu) ? 2 : 0;
+            for (uint32_t k = 0; k < 8; ++k) {
+                if (e0 + k >= Suse) continue;
+                const bool killed = ((kw[k >> 2] >> (8 * (k & 3u))) & 0xffu) != 0u;
+                if (killed) st[k >> 2] |= 2u << (8 * (k & 3u));
+                else keepm |= 1u << k;
+            }
+            *reinterpret_cast<uint2*>(s.state + e0) = make_uint2(st[0], st[1]);
         }
         const uint32_t P = ld_cg(a.ctrl + 2 + p);
         // a CTA's list overflowed, or the window's is too long for rounds
@@ -825,19 +849,23 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         if (!over && P == 0u) {
             // no conflict inside the window: the entries no previous accept
             // rejected are the accepts
-            uint32_t keepm = 0;
-#pragma unroll
-            for (uint32_t k = 0; k < (uint32_t)kGwPerThread; ++k)
-                if (e0 + k < Suse && s.state[e0 + k] == 0) keepm |= 1u << k;
             uint32_t pos = block_exclusive_scan(s.bs, __popc(keepm), &nacc);
-            uint32_t osum = 0;   // offsets of this thread's accepts (< 8 * 2^20)
+            if (keepm) {
+                const uint4 x0 = *reinterpret_cast<const uint4*>(s.wx + e0);
+                const uint4 x1 = *reinterpret_cast<const uint4*>(s.wx + e0 + 4);
+                const uint4 f0 = *reinterpret_cast<const uint4*>(s.woff + e0);
+                const uint4 f1 = *reinterpret_cast<const uint4*>(s.woff + e0 + 4);
+                const uint32_t xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                const uint32_t fs[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+                uint32_t osum = 0;   // offsets of this thread's accepts (< 8 * 2^20)
 #pragma unroll
-            for (uint32_t k = 0; k < (uint32_t)kGwPerThread; ++k)
-                if ((keepm >> k) & 1u) {
-                    s.ax[pos++] = s.wx[e0 + k];
-                    osum += s.woff[e0 + k];
-                }
-            if (count_dense) dense += (uint64_t)__popc(keepm) * (o.N - 1 - R0) - osum;
+                for (uint32_t k = 0; k < 8; ++k)
+                    if ((keepm >> k) & 1u) {
+                        s.ax[pos++] = xs[k];
+                        osum += fs[k];
+                    }
+                if (count_dense) dense += (uint64_t)__popc(keepm) * (o.N - 1 - R0) - osum;
+            }
             __syncthreads();
         } else if (!over) {
             uint32_t Ps = P;
@@ -879,7 +907,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         surv_total += Suse;
         // the next window aims at `target` survivors at the density this one
         // had (at most twice as long), fewer where the survivors conflict
-        // densely: about kGwPairTarget pairs at this window's pair density
+        // densely: about a.pair_target pairs at this window's pair density
         {
             uint64_t tgt = a.target;
             const uint32_t Peff = over ? max(P, 4u * a.pair_target) : P;
