@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             else atomicSub(a.cnt + (v >> 2), one);
         }
     };
-    uint32_t na_prev = 0;   // this CTA's survivors in the previous window
+    uint32_t na_own = 0;   // this CTA's survivors in the current window
 
     uint64_t R0 = 0, K = 0, Kprev = 0;
     uint32_t W = a.wmin, nprev = 0;
@@ -531,11 +531,10 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             uint32_t* sx = a.seg_x + ((size_t)p * G + lb) * kGwChunk;
             uint32_t* so = a.seg_off + ((size_t)p * G + lb) * kGwChunk;
             if (a.cnt) {
-                // the previous window's survivors out of the counters, this
-                // window's in (complete at this phase's barrier)
-                count_balls(a.seg_x + ((size_t)(p ^ 1) * G + lb) * kGwChunk, true, na_prev, false);
+                // this window's survivors into the counters (complete at
+                // this phase's barrier; they come out after phase B's)
                 count_balls(s.wx, false, na, true);
-                na_prev = na;
+                na_own = na;
             }
             for (uint32_t i = tid; i < na; i += kBlock) {
                 sx[i] = s.wx[i];
@@ -811,6 +810,11 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         mark_phase(4);
 
         // ---- every CTA decides the window from the same data
+        if (a.cnt) {
+            // every CTA has probed its rows: this CTA's survivors come out
+            // of the counters, drained while the window is decided
+            count_balls(a.seg_x + ((size_t)p * G + lb) * kGwChunk, true, na_own, false);
+        }
         const uint32_t v = (uint32_t)tid < G ? ld_cg(a.pslot + (size_t)p * G + tid) : 0u;
         // kGwPerThread (8) consecutive entries per thread: their kill bytes in
         // two 4-byte loads, their states in one 8-byte store (consecutive
