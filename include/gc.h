@@ -124,8 +124,9 @@ typedef struct {
     uint32_t survivor_target; /* window sizing aims at this many survivors
                                  (gc_plan: 512 distance, 1024 bitmap; 4096
                                  lex/Gray and 2048 graded for bitmap sweeps
-                                 of >= 2^28 candidates; 4400 for the grid
-                                 strategy, whose windows end after 4096) */
+                                 of >= 2^28 candidates; 8800 for the grid
+                                 strategy, whose windows end after 8192 and
+                                 aim lower where survivors conflict densely) */
 } gc_plan_t;
 
 /* Counters filled by the sweep (device-side writes, read after sync). */
