@@ -564,37 +564,42 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
         // entry e of the window sits in the segment of the last CTA g with
         // pref[g] <= e (empty segments share their successor's prefix); a
         // thread gathers its entries four at a time
-#pragma unroll 1
-        for (uint32_t h = 0; h < (uint32_t)kGwPerThread; h += 4) {
-            uint32_t at[4];  // < 2 * grid * kGwChunk
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
-                const uint32_t e = tid + (h + k) * kBlock;
+        {
+            // segment address of entry e
+            auto seg_at = [&](uint32_t e) -> uint32_t {
                 uint32_t lo = 0, hi = G;
                 while (hi - lo > 1u) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (s.pref[mid] <= e) lo = mid;
                     else hi = mid;
                 }
-                at[k] = ((uint32_t)p * G + lo) * (uint32_t)kGwChunk + (e - s.pref[lo]);
+                return ((uint32_t)p * G + lo) * (uint32_t)kGwChunk + (e - s.pref[lo]);  // < 2 * grid * kGwChunk
+            };
+            // a thread's eight entries in two groups of four; the second
+            // group's loads go out before the first group is stored
+            uint32_t xa0 = 0, xa1 = 0, xa2 = 0, xa3 = 0, oa0 = 0, oa1 = 0, oa2 = 0, oa3 = 0;
+            uint32_t xb0 = 0, xb1 = 0, xb2 = 0, xb3 = 0, ob0 = 0, ob1 = 0, ob2 = 0, ob3 = 0;
+#define GW_LOAD(k, X, O)                                           \
+            if (tid + (k) * kBlock < Suse) {                       \
+                const uint32_t at_ = seg_at(tid + (k) * kBlock);   \
+                X = ld_cg(a.seg_x + at_);                          \
+                O = ld_cg(a.seg_off + at_);                        \
             }
-            uint32_t vx[4], vo[4];
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k)
-                if (tid + (h + k) * kBlock < Suse) {
-                    vx[k] = ld_cg(a.seg_x + at[k]);
-                    vo[k] = ld_cg(a.seg_off + at[k]);
-                }
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
-                const uint32_t e = tid + (h + k) * kBlock;
-                if (e < Suse) {
-                    s.wx[e] = vx[k];
-                    s.woff[e] = vo[k];
-                    // this CTA's rows also go to rx, contiguous
-                    if ((own >> (h + k)) & 1u) s.rx[(e - lb) / G] = vx[k];
-                }
+            GW_LOAD(0, xa0, oa0) GW_LOAD(1, xa1, oa1) GW_LOAD(2, xa2, oa2) GW_LOAD(3, xa3, oa3)
+            GW_LOAD(4, xb0, ob0) GW_LOAD(5, xb1, ob1) GW_LOAD(6, xb2, ob2) GW_LOAD(7, xb3, ob3)
+#undef GW_LOAD
+#define GW_STORE(k, X, O)                                          \
+            {                                                      \
+                const uint32_t e_ = tid + (k) * kBlock;            \
+                if (e_ < Suse) {                                   \
+                    s.wx[e_] = X;                                  \
+                    s.woff[e_] = O;                                \
+                    if ((own >> (k)) & 1u) s.rx[(e_ - lb) / G] = X; \
+                }                                                  \
             }
+            GW_STORE(0, xa0, oa0) GW_STORE(1, xa1, oa1) GW_STORE(2, xa2, oa2) GW_STORE(3, xa3, oa3)
+            GW_STORE(4, xb0, ob0) GW_STORE(5, xb1, ob1) GW_STORE(6, xb2, ob2) GW_STORE(7, xb3, ob3)
+#undef GW_STORE
         }
         // this CTA's rows: entries lb + r * G, r < rows; s.flags[r] = killed
         const uint32_t rows = Suse > lb ? (Suse - lb + G - 1) / G : 0u;
