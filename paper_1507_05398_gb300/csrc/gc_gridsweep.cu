@@ -70,6 +70,7 @@ constexpr uint32_t kGwPairSmem = 16384; // pairs a CTA takes into shared memory
 constexpr uint32_t kGwPairGlobal = 8 * kGwPairSmem;  // pairs decided by rounds over L2
 constexpr int kGwMaxCtas = kBlock;      // one count per thread in the prefix scans
 constexpr int kGwProbeBatch = 14;       // high-bit probes a lookup issues at once
+static_assert(kGwChunk <= 4 * kBlock, "a thread generates at most four ranks of its CTA's chunk");
 static_assert(kGwSurvCap <= 65536, "pairs pack two entry indices in 16 bits each");
 constexpr int kGwPerThread = kGwSurvCap / kBlock;   // window entries per thread
 static_assert(kGwSurvCap % (4 * kBlock) == 0, "threads take window entries four at a time");
@@ -497,37 +498,104 @@ __global__ void __launch_bounds__(kBlock, 1) grid_sweep_kernel(const __grid_cons
             const uint64_t chunk = (span + G - 1) / G;
             const uint64_t c0 = min(R0 + (uint64_t)lb * chunk, R0 + span);
             const uint64_t c1 = min(c0 + chunk, R0 + span);
-            uint32_t na = 0;
-            for (uint64_t t0 = c0; t0 < c1; t0 += kBlock) {
-                const uint64_t r = t0 + tid;
-                uint32_t x = 0;
-                bool keep = false;
-                if (r < c1) {
-                    keep = unrank(o, s.C, r, x);
-                            if (keep) {
-                        const uint32_t key = a.reversed ? reverse_n(x, n) : x;
-                        const uint32_t w0 = key >> 5, b = key & 31u;
-                        if (!a.probe) {
-                            keep = !((ld_cg(a.bitmap + w0) >> b) & 1u);
+            // thread tid takes the `per` consecutive ranks from c0 + tid * per
+            // (per <= 4), so one scan puts its survivors in rank order.  In
+            // the orders that list a weight class as k-subsets in numeric
+            // order (grlex, lex with a weight; grevlex reversed and backwards)
+            // the first rank is unranked and the next ones are stepped to
+            // the next (grevlex: previous) integer of the same weight.
+            const uint32_t len = (uint32_t)(c1 - c0);
+            const uint32_t per = (len + kBlock - 1) / kBlock;
+            const uint64_t rb = c0 + (uint64_t)tid * per;
+            const bool graded = o.ord == kGrlex || o.ord == kGrevlex || (o.ord == kLex && o.w >= 0);
+            const uint32_t nmask = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+            uint32_t xs[4] = {0u, 0u, 0u, 0u};
+            uint32_t candm = 0;
+            {
+                int k = 0;          // graded: weight class, index in it, subset
+                uint64_t ci = 0;
+                uint32_t y = 0;
+                auto full = [&](uint64_t r) {
+                    if (o.w >= 0) {
+                        k = o.w;
+                        ci = r;
+                    } else {
+                        k = 0;
+                        while (k < n && o.cum[k + 1] <= r) ++k;
+                        ci = r - o.cum[k];
+                    }
+                    const uint32_t m = o.ord == kGrevlex ? (uint32_t)(s.C[n][k] - 1u - ci) : (uint32_t)ci;
+                    y = comb_unrank(s.C, n, k, m);
+                };
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint64_t r = rb + j;
+                    if (j >= per || r >= c1) continue;
+                    if (!graded) {
+                        uint32_t x = 0;
+                        if (unrank(o, s.C, r, x)) {
+                            xs[j] = x;
+                            candm |= 1u << j;
+                        }
+                        continue;
+                    }
+                    if (j == 0 || ci + 1 >= (uint64_t)s.C[n][k]) {
+                        full(r);
+                    } else {
+                        ++ci;
+                        if (o.ord == kGrevlex) {
+                            // previous integer of weight k: the complement's
+                            // next one of weight n - k, complemented
+                            const uint32_t z = ~y & nmask;
+                            const uint32_t low = z & (0u - z), ripple = z + low;
+                            y = ~(ripple | (((z ^ ripple) >> 2) >> (__ffs(z) - 1))) & nmask;
                         } else {
-                            // covered iff a marked vector is within distance 1:
-                            // in the word, or this bit of a word one high bit away
-                            bool hit = (ld_cg(a.bitmap + w0) & s.lowball[1][b]) != 0u;
-                            const int nh = n > 5 ? n - 5 : 0;
-                            for (int j0 = 0; j0 < nh && !hit; j0 += kGwProbeBatch) {
-                                uint32_t v[kGwProbeBatch];
-#pragma unroll
-                                for (int u = 0; u < kGwProbeBatch; ++u)
-                                    v[u] = j0 + u < nh ? ld_cg(a.bitmap + (w0 ^ (1u << (j0 + u)))) : 0u;
-#pragma unroll
-                                for (int u = 0; u < kGwProbeBatch; ++u) hit = hit || ((v[u] >> b) & 1u);
-                            }
-                            keep = !hit;
+                            // next integer of weight k (Gosper's rule)
+                            const uint32_t low = y & (0u - y), ripple = y + low;
+                            y = ripple | (((y ^ ripple) >> 2) >> (__ffs(y) - 1));
                         }
                     }
+                    xs[j] = o.ord == kGrevlex ? reverse_n(y, n) : y;
+                    candm |= 1u << j;
                 }
-                na = block_append(s.bs, keep, x, (uint32_t)(r - R0), s.wx, s.woff, na);
             }
+            const int nh = n > 5 ? n - 5 : 0;
+            uint32_t keepm = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                if (!((candm >> j) & 1u)) continue;
+                const uint32_t x = xs[j];
+                const uint32_t key = a.reversed ? reverse_n(x, n) : x;
+                const uint32_t w0 = key >> 5, b = key & 31u;
+                bool hit;
+                if (!a.probe) {
+                    hit = ((ld_cg(a.bitmap + w0) >> b) & 1u) != 0u;
+                } else {
+                    // covered iff a marked vector is within distance 1: in
+                    // the word, or this bit of a word one high bit away
+                    hit = (ld_cg(a.bitmap + w0) & s.lowball[1][b]) != 0u;
+                    for (int j0 = 0; j0 < nh && !hit; j0 += kGwProbeBatch) {
+                        uint32_t v[kGwProbeBatch];
+#pragma unroll
+                        for (int u = 0; u < kGwProbeBatch; ++u)
+                            v[u] = j0 + u < nh ? ld_cg(a.bitmap + (w0 ^ (1u << (j0 + u)))) : 0u;
+#pragma unroll
+                        for (int u = 0; u < kGwProbeBatch; ++u) hit = hit || ((v[u] >> b) & 1u);
+                    }
+                }
+                if (!hit) keepm |= 1u << j;
+            }
+            uint32_t na = 0;
+            uint32_t pos = block_exclusive_scan(s.bs, (uint32_t)__popc(keepm), &na);
+            const uint32_t off0 = (uint32_t)(rb - R0);
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j)
+                if ((keepm >> j) & 1u) {
+                    s.wx[pos] = xs[j];
+                    s.woff[pos] = off0 + j;
+                    ++pos;
+                }
+            __syncthreads();
             uint32_t* sx = a.seg_x + ((size_t)p * G + lb) * kGwChunk;
             uint32_t* so = a.seg_off + ((size_t)p * G + lb) * kGwChunk;
             if (a.cnt) {
