@@ -16,9 +16,12 @@
 //  A. every CTA writes its share of window t-1's accepts to the output, ORs
 //     its share of their balls into the bitmap, then generates its
 //     contiguous chunk of window t from the ranks (Section 4.2 orders,
-//     closed form) and drops the candidates the bitmap covers -- it is
-//     complete up to window t-2 and holds part of window t-1.  The survivors
-//     go to the CTA's segment, in rank order.
+//     closed form; a thread takes up to four consecutive ranks, and in the
+//     orders that list a weight class as k-subsets in numeric order steps
+//     from one to the next instead of unranking each) and drops the
+//     candidates the bitmap covers -- it is complete up to window t-2 and
+//     holds part of window t-1.  The survivors go to the CTA's segment, in
+//     rank order.
 //  B. every CTA gathers the window's survivors (the first kGwSurvCap; the
 //     window is cut after them).  It probes its rows (entries i = CTA index
 //     mod grid) against the bitmap, now complete up to window t-1 -- a hit
