@@ -235,6 +235,58 @@ def test_parity_extension_relates_the_stored_n31_and_n32_codes():
     assert _parity_ext(a["last"]) == b["last"]
 
 
+def _hamming_syndrome(x, first_bit=0):
+    """Syndrome of the binary Hamming code whose parity check maps bit i of
+    the vector (value 2^i) to the column i + 1 (numpy, elementwise)."""
+    s = np.zeros_like(x)
+    for i in range(32):
+        bit = (x >> np.uint32(i)) & np.uint32(1)
+        s ^= bit * np.uint32(first_bit + i + 1)
+    return s
+
+
+def test_hamming_lexicode_closed_form_at_small_n():
+    """The d = 3 lexicode of length 2^m - 1 is the Hamming code with the
+    parity check i -> i + 1 (Section 7 names the perfect codes): checked
+    against the oracle at n = 3, 7, 15."""
+    for n in (3, 7, 15):
+        x = np.arange(1 << n, dtype=np.uint32)
+        closed = x[_hamming_syndrome(x) == 0]
+        assert closed.tolist() == oracle.greedy_ball(n, 3, "lex").tolist(), n
+
+
+def test_stored_n31_and_n32_digests_from_the_hamming_closed_form():
+    """The stored n = 31, d = 3 lex digest (oracle O2) is the Hamming
+    [31,26,3] code of the closed form above, in increasing order, and the
+    stored n = 32, d = 4 lex digest is that code with an overall parity bit
+    appended (extended Hamming [32,26,4]).  The code is built in increasing
+    order without a sort: a word is (hi << 16) | lo, and for each high part
+    the low parts are the 2048 whose syndrome cancels the high part's."""
+    import hashlib
+    rows = _large_rows()
+    lo = np.arange(1 << 16, dtype=np.uint32)
+    syn_lo = _hamming_syndrome(lo)
+    by_syn = [lo[syn_lo == v] for v in range(32)]
+    assert all(len(b) == 2048 for b in by_syn)
+    table = np.stack(by_syn)                                  # [32][2048], increasing
+    h31, h32 = hashlib.sha256(), hashlib.sha256()
+    size = 0
+    for h0 in range(0, 1 << 15, 4096):
+        hi = np.arange(h0, h0 + 4096, dtype=np.uint32)
+        syn_hi = _hamming_syndrome(hi, first_bit=16)
+        words = ((hi[:, None] << np.uint32(16)) | table[syn_hi]).reshape(-1)
+        h31.update(words.astype("<u4").tobytes())
+        par = words.copy()
+        for sh in (16, 8, 4, 2, 1):
+            par ^= par >> np.uint32(sh)
+        ext = (words << np.uint32(1)) | (par & np.uint32(1))   # < 2^32: bit 31 of words is 0
+        h32.update(ext.astype("<u4").tobytes())
+        size += words.size
+    assert size == rows[(31, 3, "lex")]["size"] == rows[(32, 4, "lex")]["size"] == 1 << 26
+    assert h31.hexdigest() == rows[(31, 3, "lex")]["sha256"]
+    assert h32.hexdigest() == rows[(32, 4, "lex")]["sha256"]
+
+
 @pytest.mark.skipif(not os.environ.get("GC_SLOW"), reason="a minute of CPU; set GC_SLOW=1")
 def test_parity_extension_of_the_n31_oracle_code_gives_the_stored_n32_digest():
     """The whole n = 31, d = 3 lex code from the oracle, extended by parity,
